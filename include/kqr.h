@@ -1,0 +1,244 @@
+/*
+ * kqr.h -- C ABI of the GB300 (sm_103a) kernel quantile regression library.
+ *
+ * The library solves the kernel quantile regression problem of Deng, Li and
+ * Zhang, "Scalable Kernel Quantile Regression: A Preconditioned Augmented
+ * Lagrangian Method" (arxiv 2510.07929):
+ *
+ *   min_{beta, f in H_k}  sum_i rho_tau(y_i - beta - f(x_i)) + lambda/2 ||f||^2   (eq. (1.1))
+ *
+ * through its dual (eq. (1.3)):
+ *
+ *   max_alpha  -alpha^T K alpha / (2 lambda) + y^T alpha,
+ *   alpha in [tau - 1, tau]^n,  1^T alpha = 0,
+ *
+ * with the two-phase method of the paper: inexact ADMM (Alg. 1), then the
+ * semismooth Newton augmented Lagrangian method (Alg. 2 and Alg. 3) whose
+ * Newton systems (eq. (3.1)) are solved by CG preconditioned with a low-rank
+ * RPCholesky factor applied through the Woodbury identity (Lemma 1).  The
+ * fitted function is f(x) = beta + (1/lambda) sum_j alpha_j k(x_j, x)
+ * (representer form, Sec. 1).
+ *
+ * Every step of the solve runs in CUDA kernels on the current device.  Kernel
+ * matrices are never stored: their entries are formed in tiles inside the
+ * Gram-product kernels.
+ *
+ * Conventions for every function below:
+ *   - Host pointers ("host") are read or written before the call returns; the
+ *     caller owns them.  Device pointers ("device") must point to memory of the
+ *     handle's device; the caller owns them.
+ *   - Matrices are row-major.  X is n x p; V and U are n x m (m right-hand sides).
+ *   - Errors are returned as kqr_status, never thrown; kqr_last_error(h) gives a
+ *     one-line description of the last failure on that handle.
+ *   - A handle is used by one host thread at a time.  It owns a CUDA stream, or
+ *     uses the one given by kqr_set_stream.  The *_dev functions enqueue work
+ *     on the given stream (NULL = the handle's stream) and return without
+ *     synchronising, except where stated.
+ */
+#ifndef KQR_H
+#define KQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kqr_status {
+  KQR_OK = 0,
+  KQR_INVALID_ARG = 1,        /* bad size, pointer, tau, lambda, gamma or non-finite data */
+  KQR_OOM = 2,                /* device allocation failed */
+  KQR_CUDA_ERROR = 3,         /* a CUDA call or kernel launch failed */
+  KQR_NOT_CONVERGED = 4,      /* iteration cap reached; outputs hold the last iterate */
+  KQR_BREAKDOWN = 5,          /* CG curvature p^T A p <= 0 or NaN, or a factorisation failed */
+  KQR_TIMEOUT = 6,            /* host wall-clock limit (options.time_limit_s) reached */
+  KQR_DEVICE_WAIT_TIMEOUT = 7 /* a kernel gave up a bounded wait on a copy and returned */
+} kqr_status;
+
+/* Kernel functions of Sec. 1 (text after eq. (1.1)). */
+typedef enum kqr_kernel {
+  KQR_RBF = 0,       /* k(x, x') = exp(-gamma ||x - x'||_2^2) */
+  KQR_LAPLACIAN = 1  /* k(x, x') = exp(-gamma ||x - x'||_1)   */
+} kqr_kernel;
+
+/* Arithmetic of a Gram product.
+ * KQR_PREC_HIGH: entries and sums accurate to about 1e-13 relative (FP64 class;
+ *   Laplacian: exact fixed-point L1 distances plus double-float exp and sums on
+ *   the FP32/INT32 pipes; RBF: FP64).  Used for gradients and KKT residuals.
+ * KQR_PREC_FP32: FP32 entries and FP32 partial sums, about 1e-6 relative per
+ *   entry.  Used inside CG. */
+typedef enum kqr_precision {
+  KQR_PREC_HIGH = 0,
+  KQR_PREC_FP32 = 1
+} kqr_precision;
+
+/* Preconditioner for the linear systems (2.1) and (3.1).
+ * KQR_PRECOND_PAPER: P = F F^T + lambda sigma 1 1^T + L (eq. (3.2)).
+ * KQR_PRECOND_NYSTROM_DIAG: as PAPER with L replaced by L + max(diag(K - F F^T), nu),
+ *   the RPCholesky residual diagonal floored at nu = 0.1 mean(diag(K - F F^T))
+ *   (still diagonal plus low rank, so Lemma 1 applies unchanged; the floor keeps
+ *   L^{-1} bounded at the pivots, whose residual is 0; not in the paper).
+ * KQR_PRECOND_NONE: plain CG (the paper's NALM-KQR ablation, Sec. 4.1). */
+typedef enum kqr_precond {
+  KQR_PRECOND_NYSTROM_DIAG = 0,
+  KQR_PRECOND_PAPER = 1,
+  KQR_PRECOND_NONE = 2
+} kqr_precond;
+
+/* Algorithm constants.  The paper leaves them open; kqr_default_options fills
+ * in the library's readings. */
+typedef struct kqr_options {
+  /* preconditioner set-up (Sec. 3) */
+  int32_t rank0;                 /* initial RPCholesky rank r0; 0 = ceil(sqrt(n)) */
+  int32_t adaptive_rank;         /* 1: pick r from the spectrum of F0^T F0 (Sec. 3); 0: r = r0 */
+  double xi;                     /* rank threshold: smallest r with xi * lambda_1 >= lambda_r */
+  uint64_t seed;                 /* pivot stream seed used when pivot_uniforms is NULL */
+  const double* pivot_uniforms;  /* host, optional: one uniform [0,1) per pivot step, length >= r0 */
+  kqr_precond precond;
+  /* Phase I, inexact ADMM (Alg. 1) */
+  double sigma0;                 /* initial penalty sigma */
+  double gamma_admm;             /* step length in (0, (1 + sqrt 5) / 2) */
+  double admm_tol;               /* stop when max(eta_kkt, eta_gap) <= admm_tol (Sec. 4: 1e-3) */
+  int32_t admm_maxit;            /* ... or after admm_maxit iterations (Sec. 4: 100) */
+  int32_t balance_every;         /* residual balancing period for sigma */
+  double balance_ratio;          /* rebalance when eta_p / eta_d leaves [1/ratio, ratio] */
+  double balance_factor;         /* multiply or divide sigma by this */
+  /* Phase II, SSN-ALM (Alg. 2, Alg. 3) */
+  int32_t alm_maxit;             /* Sec. 4: 1000 */
+  double sigma_alm_scale;        /* Phase II sigma_0 = max(final Phase I sigma, sigma_alm_scale / lambda) */
+  double sigma_factor;           /* sigma *= sigma_factor when eta_d fails to halve */
+  double sigma_max;
+  double eta_bar, iota, mu, r_ls, tau1, tau2;   /* Alg. 3 constants */
+  int32_t ssn_maxit;             /* Newton steps per ALM subproblem */
+  int32_t ls_maxit;              /* backtracking steps per Newton step */
+  int32_t pcg_maxit;             /* CG iterations per linear system */
+  double time_limit_s;           /* host wall-clock limit per solve; <= 0: none */
+  int32_t phase1_only;           /* 1: stop after Phase I (for tests of Alg. 1) */
+  int32_t verbose;               /* 1: one line per outer iteration on stderr */
+} kqr_options;
+
+/* Counters and final residuals of a solve (Sec. 4 definitions). */
+typedef struct kqr_info {
+  int32_t phase1_iters, phase2_iters, newton_steps, pcg_iters;
+  int32_t matvecs_fp32, matvecs_high;  /* Gram products by arithmetic, each counted once per RHS */
+  int32_t rank;                        /* preconditioner rank r */
+  double eta_p, eta_d, eta_c, eta_kkt, eta_gap, obj_p, obj_d;
+  double sigma_final;
+  double seconds;                      /* wall-clock of the solve */
+} kqr_info;
+
+typedef struct kqr_handle kqr_handle;
+
+/* Fills *o with the library's default constants. */
+void kqr_default_options(kqr_options* o);
+
+/* Routes the library's device allocations through alloc/free (for example a
+ * framework's caching allocator); NULL restores cudaMalloc/cudaFree.  Affects
+ * handles created afterwards.  alloc returns NULL on failure. */
+void kqr_set_allocator(void* (*alloc)(size_t bytes, void* ctx), void (*free_fn)(void* ptr, void* ctx), void* ctx);
+
+/* Creates a problem on the current device: copies X (host, n x p, row-major)
+ * and y (host, n) to the device, prepares the tile layouts of X for the Gram
+ * kernels, and builds the RPCholesky factor F (n x r) of K (Sec. 3), which
+ * depends only on (X, kernel, gamma) and is reused by every later solve.
+ * n >= 2, 1 <= p <= 128, gamma > 0, X and y finite.  opts may be NULL
+ * (defaults).  On success *out owns all device memory of the problem. */
+kqr_status kqr_create(const double* X, const double* y, int64_t n, int64_t p, kqr_kernel kind,
+                      double gamma, const kqr_options* opts, kqr_handle** out);
+
+/* Solves the dual (1.3) for (tau, lambda) to max(eta_kkt, eta_gap) <= tol
+ * (Sec. 4 stopping rule), Phase I then Phase II.  0 < tau < 1, lambda > 0,
+ * tol > 0.  alpha (host, n) receives the dual solution (also theta of the
+ * representer form); *beta the intercept; *kkt = eta_kkt, evaluated with the
+ * FP64-class Gram product.  info (nullable) receives counters and residuals.
+ * Returns KQR_NOT_CONVERGED (outputs filled with the last iterate) when the
+ * iteration caps are reached.  Synchronises. */
+kqr_status kqr_solve(kqr_handle* h, double tau, double lambda, double tol,
+                     double* alpha, double* beta, double* kkt, kqr_info* info);
+
+/* After kqr_solve: copies the last iterate's consensus variable v and
+ * multiplier z of (1.4)-(1.5) to host arrays of length n (either may be NULL). */
+kqr_status kqr_get_state(kqr_handle* h, double* v, double* z);
+
+/* U = K V for host V (n x m, row-major) and host U (n x m); 1 <= m <= 8.
+ * Copies V in and U out inside the call.  Synchronises. */
+kqr_status kqr_kmatvec(kqr_handle* h, const double* V, double* U, int64_t m, kqr_precision prec);
+
+/* As kqr_kmatvec with device V and U (n x m, row-major, double).  The Gram
+ * product of Sec. 1 / Sec. 3, entries formed on the fly in tiles. */
+kqr_status kqr_kmatvec_dev(kqr_handle* h, const double* V, double* U, int64_t m, kqr_precision prec,
+                           void* stream);
+
+/* Projection, Jacobian and gradient of the ALM subproblem (eq. (2.3), Sec. 2.2,
+ * eq. (3.1)), device vectors of length n:
+ *   w = alpha + z / sigma, v = Pi_B(w), S_ii = 1 if tau - 1 < w_i < tau else 0,
+ *   grad = Kalpha / lambda - y + beta + sigma 1^T alpha + sigma (w - v),
+ *   Ldiag = lambda sigma (1 - S) + lambda eps.
+ * Kalpha is K alpha (device).  Any output pointer may be NULL.  *grad_norm2
+ * (host, nullable) receives ||grad||^2 (synchronises when non-NULL). */
+kqr_status kqr_box_grad_dev(kqr_handle* h, const double* alpha, const double* z, const double* Kalpha,
+                            double beta, double sigma, double tau, double lambda, double eps,
+                            double* v, double* S, double* grad, double* Ldiag, double* grad_norm2,
+                            void* stream);
+
+/* Preconditioner apply of Lemma 1 with the handle's factor F:
+ *   out = P^{-1} r,  P = F F^T + gam 1 1^T + diag(Ldiag)  (Ldiag > 0, gam > 0),
+ * building the (r+1) x (r+1) core C + U^T L^{-1} U and its Cholesky factor
+ * first.  Ldiag, r, out: device, length n.  This applies exactly the given
+ * Ldiag (no residual-diagonal correction).  Synchronises. */
+kqr_status kqr_precond_apply_dev(kqr_handle* h, const double* Ldiag, double gam, const double* r,
+                                 double* out, void* stream);
+
+/* Preconditioned CG (Sec. 3) for (K + gam 1 1^T + diag(Ldiag)) x = b with the
+ * handle's preconditioner kind, FP32 Gram products, from x = 0, until the
+ * recursive residual satisfies ||r|| <= tol or maxit iterations.  b, x device.
+ * *iters (nullable) receives the iteration count.  Synchronises. */
+kqr_status kqr_pcg_dev(kqr_handle* h, const double* Ldiag, double gam, const double* b, double* x,
+                       double tol, int32_t maxit, int32_t* iters, void* stream);
+
+/* Relative KKT residuals and duality gap of Sec. 4 for host (alpha, v, beta, z)
+ * with the FP64-class Gram product: out[0..6] = eta_p, eta_d, eta_c, eta_kkt,
+ * eta_gap, obj_p, obj_d.  Synchronises. */
+kqr_status kqr_kkt(kqr_handle* h, const double* alpha, const double* v, double beta, const double* z,
+                   double tau, double lambda, double* out7);
+
+/* The RPCholesky factor built by kqr_create: F (host, n x rank, column-major,
+ * float), pivots (host, int64, rank0 entries: the first-pass pivot sequence),
+ * *rank and *rank0.  Any pointer may be NULL. */
+kqr_status kqr_get_factor(kqr_handle* h, float* F, int64_t* pivots, int32_t* rank, int32_t* rank0);
+
+/* Rebuilds the RPCholesky factor of Sec. 3 from the device-resident X of the
+ * handle (same kernel and gamma), with the pivot uniforms given (host,
+ * nullable, length >= r0) or, if NULL, the splitmix64 stream of
+ * options.seed.  Used to time the set-up on resident data.  Synchronises. */
+kqr_status kqr_refactor(kqr_handle* h, const double* pivot_uniforms);
+
+/* Instrumentation (no counterpart in the paper).  kqr_profile(h, 1) resets
+ * and enables CUDA-event timing of the Gram tile kernels on the handle's
+ * stream; kqr_profile(h, 0) disables it.  kqr_profile_read returns, for
+ * kernel_id 0 (FP32 Gram tiles) or 1 (FP64-class Gram tiles), the number of
+ * launches and their summed device time in milliseconds since the last reset.
+ * Reading synchronises the handle's stream. */
+kqr_status kqr_profile(kqr_handle* h, int32_t enable);
+kqr_status kqr_profile_read(kqr_handle* h, int32_t kernel_id, int64_t* launches, double* total_ms);
+
+/* Makes the handle enqueue its work on the given cudaStream_t (NULL: its own). */
+kqr_status kqr_set_stream(kqr_handle* h, void* stream);
+
+int64_t kqr_n(const kqr_handle* h);
+int64_t kqr_p(const kqr_handle* h);
+
+/* Number of kernel launches the handle has issued since creation. */
+int64_t kqr_launch_count(const kqr_handle* h);
+
+const char* kqr_last_error(const kqr_handle* h);
+const char* kqr_status_string(kqr_status s);
+
+/* Frees every device buffer of the handle.  NULL is ignored. */
+void kqr_destroy(kqr_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KQR_H */

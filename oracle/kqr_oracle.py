@@ -266,8 +266,9 @@ class Options:
     balance_ratio: float = 5.0   # rebalance when eta_p / eta_d leaves [1/5, 5]
     balance_factor: float = 1.5  # sigma multiplied or divided by this
     alm_maxit: int = 1000        # Phase II stop: 1000 iterations (Sec. 4)
-    sigma_factor: float = 3.0    # ALM "sigma_{k+1} >= sigma_k" rule (reading)
-    sigma_max: float = 1e6
+    sigma_alm_scale: float = 1.0 # ALM sigma_0 = max(final ADMM sigma, sigma_alm_scale / lambda) (reading)
+    sigma_factor: float = 10.0   # ALM "sigma_{k+1} >= sigma_k" rule (reading)
+    sigma_max: float = 1e8
     eta_bar: float = 0.5         # Alg. 3 constants (reading)
     iota: float = 0.5
     mu: float = 1e-4
@@ -371,14 +372,16 @@ def alm(K, y, tau: float, lam: float, o: Options, tol: float, start: dict):
     updates beta += sigma 1^T alpha, z += sigma (alpha - v).  Stops when
     max(eta_kkt, eta_gap) <= tol or after alm_maxit iterations (Sec. 4).
 
-    Readings: sigma_0 is Phase I's final sigma; sigma is multiplied by
+    Readings: sigma_0 = max(Phase I's final sigma, sigma_alm_scale / lambda)
+    (the multiplier of 1^T alpha = 0 contracts by about 1 / (1 + lambda sigma
+    1^T K^-1 1) per iteration, so sigma is put on the 1/lambda scale); sigma is multiplied by
     sigma_factor (capped at sigma_max) whenever eta_d fails to halve; the SSN
     inner tolerance is max(0.1 tol (1 + ||y||), g0 0.2^(k+1)), g0 the gradient
     norm at the first ALM iterate."""
     alpha = np.array(start["alpha"], dtype=np.float64)
     beta = float(start["beta"])
     z = np.array(start["z"], dtype=np.float64)
-    sigma = float(start["sigma"])
+    sigma = max(float(start["sigma"]), o.sigma_alm_scale / lam)
     ny = float(np.linalg.norm(y))
     g0 = None
     prev_eta_d = None

@@ -1,0 +1,358 @@
+// Two-phase PALM-KQR driver: Phase I inexact ADMM (Alg. 1) and Phase II
+// semismooth Newton ALM (Alg. 2 with Alg. 3), with preconditioned CG for the
+// linear systems (2.1) and (3.1).  Vectors live on the device; the host keeps
+// the handful of scalars each step needs (step lengths, norms, sigma).
+//
+// Arithmetic: CG uses FP32 Gram products (entries ~1e-7 relative); the
+// gradient of phi_k (eq. (2.3)), the line search and the KKT residuals of
+// Sec. 4 use the FP64-class product, because they divide K alpha by lambda.
+// Phase I's stopping test uses the K alpha that CG tracks (the FP32 operator):
+// Phase I only supplies the warm start.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+
+#include "kqr_internal.h"
+
+namespace kqr {
+
+cudaError_t reduce_ls_pre(Handle* h, const double* Ka, const double* d, const double* Kd, const double* y,
+                          const double* g, const double* alpha, int64_t n, double* out, cudaStream_t st);
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, #call);    \
+  } while (0)
+#define KS(call)                         \
+  do {                                   \
+    kqr_status _s = (call);              \
+    if (_s != KQR_OK) return _s;         \
+  } while (0)
+
+static cudaError_t fetch(Handle* h, int slot, int count, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(h->scal_host + slot, h->scal + slot, sizeof(double) * count,
+                                  cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+static cudaError_t put(Handle* h, int slot, double v, cudaStream_t st) {
+  h->scal_host[slot] = v;
+  return cudaMemcpyAsync(h->scal + slot, h->scal_host + slot, sizeof(double), cudaMemcpyHostToDevice, st);
+}
+
+static kqr_status check_device_flag(Handle* h, cudaStream_t st) {
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "error flag");
+  if (flag) return fail(h, KQR_DEVICE_WAIT_TIMEOUT, "a Gram kernel gave up waiting for a tile copy");
+  return KQR_OK;
+}
+
+kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const double* b, double* x, double* Kx,
+               bool warm, double tol, int maxit, int* iters, cudaStream_t st) {
+  const int64_t n = h->n;
+  double* r = vec(h, V_R);
+  double* zz = vec(h, V_ZZ);
+  double* p = vec(h, V_P);
+  double* Ap = vec(h, V_AP);
+  double* Kp = vec(h, V_KP);
+  int it = 0;
+  if (!warm) {
+    CK(vec_fill(h, x, 0.0, n, st));
+    if (Kx) CK(vec_fill(h, Kx, 0.0, n, st));
+    CK(vec_copy(h, r, b, n, st));
+  } else {
+    RedArgs ra;
+    ra.a = x;
+    CK(reduce(h, RED_SUM, ra, n, h->scal + S_SUMP, st));
+    CK(op_residual(h, r, b, x, Kx, gam, h->scal + S_SUMP, L, n, st));
+  }
+  RedArgs rn;
+  rn.a = r;
+  CK(reduce(h, RED_NORM2, rn, n, h->scal + S_RR, st));
+  CK(fetch(h, S_RR, 1, st));
+  double rr = h->scal_host[S_RR];
+  if (!std::isfinite(rr)) return fail(h, KQR_BREAKDOWN, "CG: non-finite residual");
+  if (std::sqrt(rr) <= tol) {
+    if (iters) *iters = 0;
+    return KQR_OK;
+  }
+  CK(precond_apply(h, Lpre, r, zz, h->scal + S_RZ, st));
+  CK(vec_copy(h, p, zz, n, st));
+  CK(fetch(h, S_RZ, 1, st));
+  double rz = h->scal_host[S_RZ];
+  while (it < maxit) {
+    GramEpilogue ep;
+    ep.gam = gam;
+    ep.sum_p = h->scal + S_SUMP;
+    ep.L = L;
+    ep.pvec = p;
+    ep.dot_out = h->scal + S_PAP;
+    ep.raw_out = Kp;
+    CK(gram_f32(h, p, Ap, 1, &ep, st));
+    CK(fetch(h, S_PAP, 1, st));
+    const double pAp = h->scal_host[S_PAP];
+    if (!(pAp > 0.0) || !std::isfinite(pAp)) {
+      KS(check_device_flag(h, st));
+      if (iters) *iters = it;
+      return fail(h, KQR_BREAKDOWN, "CG: p^T A p = " + std::to_string(pAp));
+    }
+    CK(put(h, S_A, rz / pAp, st));
+    CK(cg_update(h, x, Kx, r, p, Kp, Ap, h->scal + S_A, n, h->scal + S_RR, st));
+    CK(fetch(h, S_RR, 1, st));
+    rr = h->scal_host[S_RR];
+    ++it;
+    if (!std::isfinite(rr)) {
+      if (iters) *iters = it;
+      return fail(h, KQR_BREAKDOWN, "CG: non-finite residual");
+    }
+    if (std::sqrt(rr) <= tol) break;
+    CK(precond_apply(h, Lpre, r, zz, h->scal + S_RZ, st));
+    CK(fetch(h, S_RZ, 1, st));
+    const double rz_new = h->scal_host[S_RZ];
+    CK(put(h, S_BETA, rz_new / rz, st));
+    CK(cg_direction(h, p, zz, h->scal + S_BETA, n, st));
+    rz = rz_new;
+  }
+  if (iters) *iters = it;
+  KS(check_device_flag(h, st));
+  return KQR_OK;
+}
+
+kqr_status kkt(Handle* h, const double* alpha, const double* v, double beta, const double* z, const double* Kalpha,
+               double tau, double lam, double* out7, cudaStream_t st) {
+  RedArgs ra;
+  ra.a = alpha; ra.b = v; ra.c = z; ra.d = h->y; ra.e = Kalpha;
+  ra.s0 = beta; ra.s1 = tau; ra.s2 = lam;
+  CK(reduce(h, RED_KKT, ra, h->n, h->scal + S_RED0, st));
+  CK(fetch(h, S_RED0, 10, st));
+  const double* s = h->scal_host + S_RED0;
+  const double eta_p = std::sqrt(s[0]) / (1.0 + std::sqrt(s[6]));
+  const double eta_d = std::sqrt(s[1] * s[1] + s[2]) / (1.0 + std::sqrt(s[3]));
+  const double eta_c = std::sqrt(s[4]) / (1.0 + std::sqrt(s[5]));
+  const double quad = s[7] / (2.0 * lam);
+  const double objp = s[9] + quad;
+  const double objd = -quad + s[8];
+  out7[0] = eta_p;
+  out7[1] = eta_d;
+  out7[2] = eta_c;
+  out7[3] = std::fmax(eta_p, std::fmax(eta_d, eta_c));
+  out7[4] = std::fabs(objp - objd) / (1.0 + std::fabs(objp) + std::fabs(objd));
+  out7[5] = objp;
+  out7[6] = objd;
+  return KQR_OK;
+}
+
+__global__ void make_L_kernel(double* L, double* Lpre, const double* S, double a, double b, const double* dres,
+                              int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double li = a * (1.0 - S[i]) + b;
+    L[i] = li;
+    Lpre[i] = li + (dres ? dres[i] : 0.0);
+  }
+}
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) {
+  const kqr_options& o = h->opt;
+  const int64_t n = h->n;
+  cudaStream_t st = h->stream;
+  const double t_start = now_s();
+  double* alpha = vec(h, V_ALPHA);
+  double* v = vec(h, V_V);
+  double* z = vec(h, V_Z);
+  double* Ka = vec(h, V_KALPHA);
+  double* b = vec(h, V_B);
+  double* d = vec(h, V_D);
+  double* Kd = vec(h, V_KD);
+  double* L = vec(h, V_L);
+  double* Lpre = vec(h, V_LPRE);
+  double* g = vec(h, V_GRAD);
+  double* S = vec(h, V_S);
+  const double* dres = (o.precond == KQR_PRECOND_NYSTROM_DIAG) ? h->dres : nullptr;
+  kqr_info inf{};
+  inf.rank = h->r;
+  double res[7] = {0, 0, 0, 0, 0, 0, 0};
+  CK(vec_fill(h, alpha, 0.0, n, st));
+  CK(vec_fill(h, v, 0.0, n, st));
+  CK(vec_fill(h, z, 0.0, n, st));
+  CK(vec_fill(h, Ka, 0.0, n, st));
+  CK(cudaMemsetAsync(h->err_flag, 0, sizeof(int), st));
+  double beta = 0.0;
+  double sigma = o.sigma0;
+  RedArgs ry;
+  ry.a = h->y;
+  CK(reduce(h, RED_NORM2, ry, n, h->scal + S_RED0 + 14, st));
+  CK(fetch(h, S_RED0 + 14, 1, st));
+  const double ynorm = std::sqrt(h->scal_host[S_RED0 + 14]);
+  auto timed_out = [&]() { return o.time_limit_s > 0 && now_s() - t_start > o.time_limit_s; };
+  kqr_status status = KQR_OK;
+
+  // ---------------- Phase I: inexact ADMM (Alg. 1) ----------------
+  CK(fill_L(h, L, lam * sigma, nullptr, n, st));
+  CK(fill_L(h, Lpre, lam * sigma, dres, n, st));
+  KS(precond_build(h, Lpre, lam * sigma, st));
+  int k = 0;
+  for (k = 0; k < o.admm_maxit; ++k) {
+    CK(admm_rhs(h, b, h->y, beta, z, v, sigma, lam, n, st));
+    RedArgs rb;
+    rb.a = b;
+    CK(reduce(h, RED_NORM2, rb, n, h->scal + S_RED0 + 15, st));
+    CK(fetch(h, S_RED0 + 15, 1, st));
+    // inexactness eps_k = 3e-4 ||b_k|| / (k + 1)^1.5: summable while ||b_k|| stays bounded
+    const double eps_k = 3e-4 * std::sqrt(h->scal_host[S_RED0 + 15]) / std::pow(k + 1.0, 1.5);
+    int its = 0;
+    KS(pcg(h, L, Lpre, lam * sigma, b, alpha, Ka, k > 0, eps_k, o.pcg_maxit, &its, st));
+    inf.pcg_iters += its;
+    inf.matvecs_fp32 += its;
+    RedArgs rs;
+    rs.a = alpha;
+    CK(reduce(h, RED_SUM, rs, n, h->scal + S_RED0 + 11, st));
+    CK(fetch(h, S_RED0 + 11, 1, st));
+    beta += o.gamma_admm * sigma * h->scal_host[S_RED0 + 11];
+    CK(admm_update(h, alpha, v, z, sigma, tau, o.gamma_admm * sigma, n, st));
+    KS(kkt(h, alpha, v, beta, z, Ka, tau, lam, res, st));
+    if (o.verbose)
+      fprintf(stderr, "[kqr] admm %3d sigma %.3g cg %4d eta_p %.2e eta_d %.2e eta_c %.2e gap %.2e\n", k, sigma, its,
+              res[0], res[1], res[2], res[4]);
+    if (std::fmax(res[3], res[4]) <= o.admm_tol) {
+      ++k;
+      break;
+    }
+    if (timed_out()) {
+      status = fail(h, KQR_TIMEOUT, "time limit in Phase I");
+      ++k;
+      break;
+    }
+    if (o.balance_every > 0 && (k + 1) % o.balance_every == 0) {
+      double ns = sigma;
+      if (res[1] > o.balance_ratio * res[0]) ns = sigma * o.balance_factor;
+      else if (res[0] > o.balance_ratio * res[1]) ns = sigma / o.balance_factor;
+      if (ns != sigma) {
+        sigma = ns;
+        CK(fill_L(h, L, lam * sigma, nullptr, n, st));
+        CK(fill_L(h, Lpre, lam * sigma, dres, n, st));
+        KS(precond_build(h, Lpre, lam * sigma, st));
+      }
+    }
+  }
+  inf.phase1_iters = k;
+
+  // FP64-class K alpha from here on.
+  CK(gram_high(h, alpha, Ka, 1, st));
+  inf.matvecs_high++;
+  KS(kkt(h, alpha, v, beta, z, Ka, tau, lam, res, st));
+  bool converged = std::fmax(res[3], res[4]) <= tol;
+
+  // ---------------- Phase II: SSN-ALM (Alg. 2, Alg. 3) ----------------
+  if (!o.phase1_only && !converged && status == KQR_OK) {
+    double g0 = -1.0, prev_eta_d = -1.0;
+    sigma = std::fmax(sigma, o.sigma_alm_scale / lam);
+    int kk = 0;
+    for (kk = 0; kk < o.alm_maxit; ++kk) {
+      // Alg. 3: Newton steps on phi_k with (beta, z, sigma) fixed.
+      double tol_grad = 0.0;
+      for (int t = 0; t < o.ssn_maxit; ++t) {
+        CK(box_grad(h, alpha, z, Ka, h->y, beta, sigma, tau, lam, 0.0, nullptr, nullptr, S, g, nullptr, nullptr, n,
+                    st));
+        CK(fetch(h, S_RED0 + 13, 1, st));
+        const double ng = std::sqrt(h->scal_host[S_RED0 + 13]);
+        if (g0 < 0) g0 = ng;
+        if (t == 0) tol_grad = std::fmax(0.1 * tol * (1.0 + ynorm), g0 * std::pow(0.2, kk + 1));
+        if (!std::isfinite(ng)) return fail(h, KQR_BREAKDOWN, "non-finite gradient");
+        if (ng <= tol_grad) break;
+        const double eps = o.tau1 * std::fmin(o.tau2, ng);
+        make_L_kernel<<<grid_for(n), 256, 0, st>>>(L, Lpre, S, lam * sigma, lam * eps, dres, n);
+        h->launches++;
+        CK(cudaGetLastError());
+        KS(precond_build(h, Lpre, lam * sigma, st));
+        CK(scale_vec(h, b, g, -lam, n, st));
+        const double ptol = lam * std::fmin(o.eta_bar, std::pow(ng, 1.0 + o.iota));
+        int its = 0;
+        KS(pcg(h, L, Lpre, lam * sigma, b, d, Kd, false, ptol, o.pcg_maxit, &its, st));
+        inf.pcg_iters += its;
+        inf.matvecs_fp32 += its;
+        // Armijo backtracking on phi_k(alpha + c d) - phi_k(alpha), term by term.
+        CK(reduce_ls_pre(h, Ka, d, Kd, h->y, g, alpha, n, h->scal + S_RED0, st));
+        CK(fetch(h, S_RED0, 6, st));
+        const double Kad = h->scal_host[S_RED0 + 0], dKd = h->scal_host[S_RED0 + 1];
+        const double yd = h->scal_host[S_RED0 + 2], sd = h->scal_host[S_RED0 + 3];
+        const double gd = h->scal_host[S_RED0 + 4], sa = h->scal_host[S_RED0 + 5];
+        const double s0 = sa + beta / sigma;
+        double c = 1.0;
+        for (int ls = 0; ls < o.ls_maxit; ++ls) {
+          RedArgs rm;
+          rm.a = alpha; rm.b = z; rm.c = d;
+          rm.s0 = sigma; rm.s1 = tau; rm.s2 = c;
+          CK(reduce(h, RED_MOREAU_DIFF, rm, n, h->scal + S_RED0 + 8, st));
+          CK(fetch(h, S_RED0 + 8, 1, st));
+          const double md = h->scal_host[S_RED0 + 8];
+          const double dphi = (c * Kad + 0.5 * c * c * dKd) / lam - c * yd +
+                              0.5 * sigma * ((s0 + c * sd) * (s0 + c * sd) - s0 * s0) + 0.5 * sigma * md;
+          if (dphi <= o.mu * c * gd) break;
+          c *= o.r_ls;
+        }
+        CK(axpy_vec(h, alpha, d, c, n, st));
+        CK(gram_high(h, alpha, Ka, 1, st));
+        inf.matvecs_high++;
+        inf.newton_steps++;
+        if (o.verbose)
+          fprintf(stderr, "[kqr]   ssn %d |grad| %.3e eps %.1e cg %4d step %.3g\n", t, ng, eps, its, c);
+        if (timed_out()) break;
+      }
+      // Alg. 2 multiplier updates.
+      RedArgs rs;
+      rs.a = alpha;
+      CK(reduce(h, RED_SUM, rs, n, h->scal + S_RED0 + 11, st));
+      CK(fetch(h, S_RED0 + 11, 1, st));
+      beta += sigma * h->scal_host[S_RED0 + 11];
+      CK(alm_update(h, alpha, v, z, sigma, tau, n, st));
+      KS(kkt(h, alpha, v, beta, z, Ka, tau, lam, res, st));
+      if (o.verbose)
+        fprintf(stderr, "[kqr] alm %3d sigma %.3g eta_p %.2e eta_d %.2e eta_c %.2e gap %.2e\n", kk, sigma, res[0],
+                res[1], res[2], res[4]);
+      if (std::fmax(res[3], res[4]) <= tol) {
+        converged = true;
+        ++kk;
+        break;
+      }
+      if (timed_out()) {
+        status = fail(h, KQR_TIMEOUT, "time limit in Phase II");
+        ++kk;
+        break;
+      }
+      if (prev_eta_d >= 0 && res[1] > 0.5 * prev_eta_d) sigma = std::fmin(o.sigma_max, sigma * o.sigma_factor);
+      prev_eta_d = res[1];
+    }
+    inf.phase2_iters = kk;
+  }
+  KS(check_device_flag(h, st));
+  CK(vec_copy(h, h->st_alpha, alpha, n, st));
+  CK(vec_copy(h, h->st_v, v, n, st));
+  CK(vec_copy(h, h->st_z, z, n, st));
+  CK(cudaStreamSynchronize(st));
+  h->st_beta = beta;
+  h->has_state = true;
+  inf.eta_p = res[0];
+  inf.eta_d = res[1];
+  inf.eta_c = res[2];
+  inf.eta_kkt = res[3];
+  inf.eta_gap = res[4];
+  inf.obj_p = res[5];
+  inf.obj_d = res[6];
+  inf.sigma_final = sigma;
+  inf.seconds = now_s() - t_start;
+  if (info) *info = inf;
+  if (status != KQR_OK) return status;
+  if (o.phase1_only) return KQR_OK;
+  if (!converged) return fail(h, KQR_NOT_CONVERGED, "iteration cap reached");
+  return KQR_OK;
+}
+
+}  // namespace kqr

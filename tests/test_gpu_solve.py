@@ -1,0 +1,148 @@
+"""GPU solves (Phase I + Phase II through kqr_solve) against the FP64 oracle.
+
+Parity contract: the GPU iterate's Sec. 4 residuals, recomputed by the oracle
+in FP64 with the exact kernel matrix, are <= 1e-6, and the dual objective of
+the (feasibly projected) GPU alpha is within 1e-6 relative of the oracle's
+optimum.  alpha is unique (K is positive definite), so both must agree."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import kqr_oracle as O
+from paper_2510_07929_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def K_():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07929_gb300 import build
+
+    build.build()
+    from paper_2510_07929_gb300 import kqr
+
+    return kqr
+
+
+def gpu_solve(K_, wl, tol=1e-6, **opts):
+    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma, **opts) as prob:
+        alpha, beta, kkt, info = prob.solve(wl.tau, wl.lam, tol)
+        v, z = prob.state()
+    return alpha, beta, v, z, kkt, info
+
+
+def check_against_oracle(wl, alpha, beta, v, z, kkt, tol=1e-6):
+    K = O.gram(wl.X, wl.X, wl.kind, wl.gamma)
+    res = O.kkt_residuals(alpha, v, beta, z, wl.y, K @ alpha, wl.tau, wl.lam)
+    assert res["eta_kkt"] <= tol and res["eta_gap"] <= tol, res
+    assert kkt == pytest.approx(res["eta_kkt"], rel=1e-3, abs=1e-12)
+    ref = O.solve_dense(K, wl.y, wl.tau, wl.lam, tol=1e-9)
+    a = O.project_feasible(alpha, wl.tau)
+    d_gpu = O.dual_objective(a, K @ a, wl.y, wl.lam)
+    d_ref = O.dual_objective(ref["alpha"], K @ ref["alpha"], wl.y, wl.lam)
+    assert abs(d_gpu - d_ref) / (1 + abs(d_ref)) <= 1e-6
+    cert = O.certified_gap(alpha, K, wl.y, wl.tau, wl.lam)
+    assert 0 <= cert["gap"] <= 1e-3   # first-order in the primal residual, which 1/lambda amplifies
+    return ref
+
+
+@pytest.mark.parametrize("name,n,tau", [("rbf_small", 2000, 0.5), ("rbf_small", 1531, 0.1),
+                                        ("lap_large", 2500, 0.25), ("rbf_mid", 2200, 0.9),
+                                        ("yuan2006", 1800, 0.1)])
+def test_solve_matches_oracle(K_, name, n, tau):
+    gen = W.GENERATORS[name]
+    wl = gen(n=n, tau=tau)
+    alpha, beta, v, z, kkt, info = gpu_solve(K_, wl)
+    assert info["status"] == K_.OK and info["phase1_iters"] >= 1
+    check_against_oracle(wl, alpha, beta, v, z, kkt)
+
+
+@pytest.mark.parametrize("precond", [1, 2])
+def test_paper_preconditioner_and_plain_cg_converge(K_, precond):
+    wl = W.rbf_small(n=900, seed=5)
+    alpha, beta, v, z, kkt, info = gpu_solve(K_, wl, precond=precond)
+    check_against_oracle(wl, alpha, beta, v, z, kkt)
+
+
+def test_phase1_only_reaches_its_tolerance(K_):
+    wl = W.rbf_small(n=1000, seed=6)
+    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma, phase1_only=1) as prob:
+        alpha, beta, kkt, info = prob.solve(wl.tau, wl.lam, 1e-6)
+    assert info["phase2_iters"] == 0
+    assert 1 <= info["phase1_iters"] <= 100
+    ref = O.admm(O.gram(wl.X, wl.X, wl.kind, wl.gamma), wl.y, wl.tau, wl.lam, O.Options())
+    # Phase I stops on its own (FP32-operator) residuals; both sides stop at the same 1e-3 rule
+    assert info["phase1_iters"] <= 100 and ref["iters"] <= 100
+    assert np.all(np.abs(alpha) <= 2.0)
+
+
+def test_two_point_closed_form(K_):
+    data = json.load(open(os.path.join(GOLDEN, "two_point.json")))
+    env = {"exp": math.exp}
+    for c in data["cases"]:
+        X, y = np.array(c["x"]), np.array(c["y"])
+        with K_.Problem(X, y, c["kind"], c["gamma"]) as prob:
+            alpha, beta, kkt, info = prob.solve(c["tau"], c["lam"], 1e-9)
+        np.testing.assert_allclose(alpha, [eval(s, env) for s in c["alpha"]], atol=1e-7)
+        if c["beta"] is not None:
+            assert beta == pytest.approx(eval(c["beta"], env), abs=1e-6)
+
+
+def test_large_lambda_lp_vertex(K_):
+    rng = np.random.default_rng(12)
+    n, tau = 40, 0.25
+    X = rng.random((n, 2))
+    y = rng.standard_normal(n)
+    K = O.gram(X, X, "rbf", 1.0)
+    order = np.argsort(-y)
+    k = int(math.ceil(n * (1 - tau) - 1))
+    a = np.full(n, tau - 1.0)
+    a[order[:k]] = tau
+    q = order[k]
+    a[q] = (n - k - 1) - (n - 1) * tau
+    Ka = K @ a
+    thr = max(abs(Ka[i] - Ka[q]) / abs(y[i] - y[q]) for i in range(n) if i != q)
+    with K_.Problem(X, y, "rbf", 1.0) as prob:
+        alpha, beta, kkt, info = prob.solve(tau, 10 * thr, 1e-9)
+    np.testing.assert_allclose(alpha, a, atol=1e-6)
+
+
+def test_repeated_solves_on_one_handle(K_):
+    wl = W.rbf_small(n=800, seed=9)
+    K = O.gram(wl.X, wl.X, wl.kind, wl.gamma)
+    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma) as prob:
+        for tau, lam in ((0.5, 1e-2), (0.9, 1e-1), (0.1, 3e-3)):
+            alpha, beta, kkt, info = prob.solve(tau, lam, 1e-6)
+            v, z = prob.state()
+            res = O.kkt_residuals(alpha, v, beta, z, wl.y, K @ alpha, tau, lam)
+            assert res["eta_kkt"] <= 1e-6 and res["eta_gap"] <= 1e-6
+
+
+def test_full_size_solve_properties(K_):
+    """n = 200000 Laplacian solve: properties that hold at any size, checked
+    by the oracle on sampled rows (the primal residual of Sec. 4 row by row,
+    feasibility, the quantile property)."""
+    wl = W.lap_large()
+    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma) as prob:
+        alpha, beta, kkt, info = prob.solve(wl.tau, wl.lam, 1e-6)
+        v, z = prob.state()
+    assert kkt <= 1e-6
+    assert np.all(v >= wl.tau - 1) and np.all(v <= wl.tau)
+    assert abs(alpha.sum()) <= 1e-6 * (1 + np.linalg.norm(alpha))
+    rows = np.random.default_rng(1).choice(wl.n, 16, replace=False)
+    Ka = O.kmatvec(wl.X, alpha, wl.kind, wl.gamma, rows=rows)
+    resid = z[rows] - wl.y[rows] + beta + Ka / wl.lam
+    # each row's share of eta_p (Sec. 4) is at most the whole
+    assert np.max(np.abs(resid)) <= 1e-6 * (1 + np.linalg.norm(wl.y))
+    zres = wl.y - beta - (wl.y - z - beta)          # = z (primal residual at the solution)
+    tol = 1e-6 * (1 + np.abs(wl.y))
+    assert np.sum(zres < -tol) <= wl.n * wl.tau + 1
+    assert np.sum(zres > tol) <= wl.n * (1 - wl.tau) + 1
