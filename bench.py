@@ -39,12 +39,13 @@ REF_PRODUCTS_PER_SOLVE = 300
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lap_large")
     ap.add_argument("--n", type=int, default=0, help="override n (testing only)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--rank0", type=int, default=1024, help="initial RPCholesky rank (library default: ceil(sqrt n))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verbose", action="store_true")
@@ -182,7 +183,8 @@ def run_ours(args):
     from paper_2510_07929_gb300 import kqr
 
     wl = workload(args, seed=rank)
-    prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, verbose=1 if args.verbose else 0)
+    opts = dict(rank0=args.rank0, verbose=1 if args.verbose else 0)
+    prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, **opts)
     stream = torch.cuda.Stream()
     prob.set_stream(stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -201,6 +203,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     step_ms = []
+    setup_ms = []
     kkts = []
     barrier()
     t_wall0 = time.perf_counter()
@@ -209,11 +212,15 @@ def run_ours(args):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        em = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, _, kkt, info = step()
+        prob.refactor()
+        em.record(stream)
+        _, _, kkt, info = prob.solve(wl.tau, wl.lam, args.tol)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
+        setup_ms.append(e0.elapsed_time(em))
         kkts.append(kkt)
         infos.append(info)
     barrier()
@@ -244,7 +251,7 @@ def run_ours(args):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with kqr.Problem(Xp.numpy(), yp.numpy(), wl.kind, wl.gamma) as p2:
+            with kqr.Problem(Xp.numpy(), yp.numpy(), wl.kind, wl.gamma, rank0=args.rank0) as p2:
                 alpha, beta, kkt2, _ = p2.solve(wl.tau, wl.lam, args.tol)
             torch.cuda.synchronize()
             e2e_s.append(time.perf_counter() - t0)
@@ -280,14 +287,15 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
-            "config": {"workload": describe(wl, args), "n": n, "p": p, "kernel": wl.kind,
+            "config": {"workload": describe(wl, args), "n": n, "p": p, "kernel": wl.kind, "rank0": args.rank0,
+                       "xi": 1e-6, "preconditioner": "RPCholesky + floored residual diagonal (Woodbury)",
                        "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1gpu"},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
             "high_precision_gram": hp,
             "solve": {"kkt": max(kkts), "phase1_iters": last["phase1_iters"], "alm_iters": last["phase2_iters"],
                       "newton_steps": last["newton_steps"], "cg_iters": last["pcg_iters"],
                       "gram_fp32": last["matvecs_fp32"], "gram_high": last["matvecs_high"], "rank": last["rank"],
-                      "eta_gap": last["eta_gap"], "wall_s": t_wall}}
+                      "eta_gap": last["eta_gap"], "wall_s": t_wall, "setup_s": sum(setup_ms) / 1e3 / args.steps}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per_mv, nrows, dt = oracle_matvec_seconds(wl, rows=96 if n >= 100000 else min(n, 2000))
         products = last["matvecs_fp32"] + last["matvecs_high"]

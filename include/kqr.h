@@ -92,7 +92,7 @@ typedef struct kqr_options {
   /* preconditioner set-up (Sec. 3) */
   int32_t rank0;                 /* initial RPCholesky rank r0; 0 = ceil(sqrt(n)) */
   int32_t adaptive_rank;         /* 1: pick r from the spectrum of F0^T F0 (Sec. 3); 0: r = r0 */
-  double xi;                     /* rank threshold: smallest r with xi * lambda_1 >= lambda_r */
+  double xi;                     /* rank threshold: smallest r with xi * lambda_1 >= lambda_r (default 1e-6) */
   uint64_t seed;                 /* pivot stream seed used when pivot_uniforms is NULL */
   const double* pivot_uniforms;  /* host, optional: one uniform [0,1) per pivot step, length >= r0 */
   kqr_precond precond;
@@ -100,6 +100,7 @@ typedef struct kqr_options {
   double sigma0;                 /* initial penalty sigma */
   double gamma_admm;             /* step length in (0, (1 + sqrt 5) / 2) */
   double admm_tol;               /* stop when max(eta_kkt, eta_gap) <= admm_tol (Sec. 4: 1e-3) */
+  double admm_cg_rtol;           /* inexactness eps_k = admm_cg_rtol ||b_k|| / (k + 1)^1.5 (summable) */
   int32_t admm_maxit;            /* ... or after admm_maxit iterations (Sec. 4: 100) */
   int32_t balance_every;         /* residual balancing period for sigma */
   double balance_ratio;          /* rebalance when eta_p / eta_d leaves [1/ratio, ratio] */

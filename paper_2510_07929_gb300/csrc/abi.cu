@@ -286,13 +286,14 @@ void kqr_default_options(kqr_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->rank0 = 0;
   o->adaptive_rank = 1;
-  o->xi = 1e-3;
+  o->xi = 1e-6;
   o->seed = 12345;
   o->pivot_uniforms = nullptr;
   o->precond = KQR_PRECOND_NYSTROM_DIAG;
   o->sigma0 = 1.0;
   o->gamma_admm = 1.618;
   o->admm_tol = 1e-3;
+  o->admm_cg_rtol = 3e-4;
   o->admm_maxit = 100;
   o->balance_every = 5;
   o->balance_ratio = 5.0;

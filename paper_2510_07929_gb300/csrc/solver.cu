@@ -205,8 +205,8 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
     rb.a = b;
     CK(reduce(h, RED_NORM2, rb, n, h->scal + S_RED0 + 15, st));
     CK(fetch(h, S_RED0 + 15, 1, st));
-    // inexactness eps_k = 3e-4 ||b_k|| / (k + 1)^1.5: summable while ||b_k|| stays bounded
-    const double eps_k = 3e-4 * std::sqrt(h->scal_host[S_RED0 + 15]) / std::pow(k + 1.0, 1.5);
+    // inexactness eps_k = admm_cg_rtol ||b_k|| / (k + 1)^1.5: summable while ||b_k|| stays bounded
+    const double eps_k = o.admm_cg_rtol * std::sqrt(h->scal_host[S_RED0 + 15]) / std::pow(k + 1.0, 1.5);
     int its = 0;
     KS(pcg(h, L, Lpre, lam * sigma, b, alpha, Ka, k > 0, eps_k, o.pcg_maxit, &its, st));
     inf.pcg_iters += its;

@@ -30,7 +30,7 @@ class Options(ctypes.Structure):
         ("rank0", ctypes.c_int32), ("adaptive_rank", ctypes.c_int32), ("xi", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("pivot_uniforms", ctypes.POINTER(ctypes.c_double)),
         ("precond", ctypes.c_int32),
-        ("sigma0", ctypes.c_double), ("gamma_admm", ctypes.c_double), ("admm_tol", ctypes.c_double),
+        ("sigma0", ctypes.c_double), ("gamma_admm", ctypes.c_double), ("admm_tol", ctypes.c_double), ("admm_cg_rtol", ctypes.c_double),
         ("admm_maxit", ctypes.c_int32), ("balance_every", ctypes.c_int32), ("balance_ratio", ctypes.c_double),
         ("balance_factor", ctypes.c_double),
         ("alm_maxit", ctypes.c_int32), ("sigma_alm_scale", ctypes.c_double), ("sigma_factor", ctypes.c_double), ("sigma_max", ctypes.c_double),

@@ -60,5 +60,5 @@ def test_options_struct_layout_matches_c(lib_path):
     from paper_2510_07929_gb300 import kqr
 
     o = kqr.default_options()
-    assert o.xi == 1e-3 and o.seed == 12345 and o.gamma_admm == 1.618 and o.sigma_factor == 10.0
+    assert o.xi == 1e-6 and o.seed == 12345 and o.gamma_admm == 1.618 and o.sigma_factor == 10.0
     assert o.tau1 == 1e-2 and o.tau2 == 1e-1 and o.pcg_maxit == 1000 and o.verbose == 0 and o.sigma_alm_scale == 1.0

@@ -93,7 +93,7 @@ def test_rpcholesky_factor_and_rank_match_oracle(K_, kind, n, p):
     wl = W.rbf_small(n=n, p=p) if kind == "rbf" else W.lap_large(n=n, p=p)
     r0 = int(np.ceil(np.sqrt(n)))
     u = W.pivot_uniforms(r0, seed=77)
-    with K_.Problem(wl.X, wl.y, kind, wl.gamma, pivot_uniforms=u) as prob:
+    with K_.Problem(wl.X, wl.y, kind, wl.gamma, pivot_uniforms=u, xi=1e-3) as prob:
         F, piv, r, rr0 = prob.factor()
     K = O.gram(wl.X, wl.X, kind, wl.gamma)
     F0, piv_o = O.rpcholesky(lambda s: K[:, s], np.diag(K), r0, u)
