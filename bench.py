@@ -33,7 +33,7 @@ SM_MAX_MHZ = 2070.0
 # Gram products (FP32 + FP64-class) of one solve of the default workload with
 # the library's default constants; the reference arm, which cannot run the
 # solver, scales the oracle's per-product time by it.
-REF_PRODUCTS_PER_SOLVE = 300
+REF_PRODUCTS_PER_SOLVE = 330
 
 
 def parse():
@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "gram"],
+                    help="gram: time --matvecs FP32 and FP64-class Gram products only (kernel profiling)")
+    ap.add_argument("--matvecs", type=int, default=3)
     return ap.parse_args()
 
 
@@ -311,10 +314,40 @@ def run_ours(args):
     return 0
 
 
+def run_gram(args):
+    """Kernel-only timing of the Gram products on the resident problem."""
+    import torch
+
+    from paper_2510_07929_gb300 import build
+
+    build.build()
+    from paper_2510_07929_gb300 import kqr
+
+    wl = workload(args)
+    prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, rank0=args.rank0)
+    V = torch.from_numpy(np.random.default_rng(0).standard_normal(wl.n)).cuda()
+    U = torch.empty_like(V)
+    out = {"mode": "gram", "config": {"workload": describe(wl, args)}}
+    for name, prec in (("fp32", kqr.PREC_FP32), ("high", kqr.PREC_HIGH)):
+        prob.kmatvec_dev(V, U, prec)
+        torch.cuda.synchronize()
+        prob.profile(True)
+        for _ in range(args.matvecs):
+            prob.kmatvec_dev(V, U, prec)
+        cnt, ms = prob.profile_read(0 if prec == kqr.PREC_FP32 else 1)
+        prob.profile(False)
+        out[name] = {"launches": cnt, "avg_ms": ms / max(cnt, 1)}
+    prob.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "gram":
+        return run_gram(args)
     return run_ours(args)
 
 
