@@ -171,6 +171,34 @@ kqr_status kqr_kmatvec(kqr_handle* h, const double* V, double* U, int64_t m, kqr
 kqr_status kqr_kmatvec_dev(kqr_handle* h, const double* V, double* U, int64_t m, kqr_precision prec,
                            void* stream);
 
+/* FP32 Gram product U = K V (as kqr_kmatvec_dev with KQR_PREC_FP32) that
+ * allocates no device memory during the call.  The paper has no counterpart.
+ *
+ * Some callers cannot allocate device memory at the moment they need a
+ * product: a process whose device memory is fully reserved up front by a pool
+ * (a further cudaMalloc fails or fragments it), code running inside another
+ * framework's allocator or memory-pressure callback (re-entering an allocator
+ * there can deadlock), or a latency-critical loop that must not pay the
+ * implicit device synchronisation of cudaMalloc and cudaFree.  This entry
+ * point keeps its scratch (the FP32 copy of V and per-split partial sums) in a
+ * fixed 32 MiB static device array instead; every GPU that loads the library
+ * holds that array until the process exits.  The handle itself (kqr_create)
+ * is set up beforehand as usual.
+ *
+ * V and U are device arrays (n x m, row-major, double), 1 <= m <= 8; the
+ * handle's device must be the current device.  A problem whose scratch need,
+ * ceil256(ldn * M * 4) + splits * ldn * M * 4 bytes (ldn = n rounded up to 128,
+ * M = m rounded up to 1, 2, 4 or 8, splits = the column splits of the launch),
+ * exceeds 32 MiB is rejected with KQR_INVALID_ARG and a message giving the
+ * sizes (about n <= 500000 rows at m = 8).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call shares the one array and each call
+ * overwrites it completely, so two calls that overlap on the GPU (on different
+ * streams, or different handles of the same device) race and both results are
+ * undefined: serialise them.  Enqueues on `stream` (NULL: the handle's) and
+ * returns without synchronising. */
+kqr_status kqr_kmatvec_fp32_noalloc_dev(kqr_handle* h, const double* V, double* U, int64_t m, void* stream);
+
 /* Projection, Jacobian and gradient of the ALM subproblem (eq. (2.3), Sec. 2.2,
  * eq. (3.1)), device vectors of length n:
  *   w = alpha + z / sigma, v = Pi_B(w), S_ii = 1 if tau - 1 < w_i < tau else 0,

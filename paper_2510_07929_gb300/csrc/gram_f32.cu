@@ -295,4 +295,58 @@ cudaError_t gram_f32(Handle* h, const double* V, double* U, int m, const GramEpi
   return cudaGetLastError();
 }
 
+// Same product as gram_f32 (no CG epilogue), with the FP32 copy of V and the
+// per-split partial sums placed in caller-provided scratch instead of handle
+// buffers.  *need receives the scratch bytes this (n, m) requires; when cap is
+// smaller nothing is launched and cudaErrorInvalidValue is returned.
+template <int KIND, int M>
+static cudaError_t launch_tiles_into(Handle* h, int splits, int tiles_per_split, const float* v32, float* part,
+                                     cudaStream_t st) {
+  const int row_tiles = (int)(h->ldn / kTile);
+  const size_t smem = f32_smem_bytes((int)h->p, M);
+  auto kern = gram_f32_kernel<KIND, M>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(row_tiles, splits), kThreads, smem, st>>>(h->tm_xs32, h->nrm32, v32, part, (int)h->p, (int)h->ldn,
+                                                        tiles_per_split, row_tiles, h->err_flag);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+template <int M>
+static cudaError_t launch_kind_into(Handle* h, int splits, int tps, const float* v32, float* part, cudaStream_t st) {
+  return h->kind == KQR_LAPLACIAN ? launch_tiles_into<KIND_LAP, M>(h, splits, tps, v32, part, st)
+                                  : launch_tiles_into<KIND_RBF, M>(h, splits, tps, v32, part, st);
+}
+
+cudaError_t gram_f32_scratch(Handle* h, const double* V, double* U, int m, unsigned char* scratch, size_t cap,
+                             size_t* need, cudaStream_t st) {
+  const int M = m <= 1 ? 1 : (m <= 2 ? 2 : (m <= 4 ? 4 : 8));
+  int splits, tps;
+  pick_splits(h, M <= 2 ? 2 : 1, &splits, &tps);
+  const size_t vbytes = ((size_t)h->ldn * M * sizeof(float) + 255) / 256 * 256;
+  const size_t pbytes = (size_t)splits * h->ldn * M * sizeof(float);
+  *need = vbytes + pbytes;
+  if (*need > cap) return cudaErrorInvalidValue;
+  float* v32 = reinterpret_cast<float*>(scratch);
+  float* part = reinterpret_cast<float*>(scratch + vbytes);
+  // to_f32_kernel writes all ldn * M entries and the tile kernel writes every
+  // (split, row) partial, so nothing read here is left over from an earlier call.
+  to_f32_kernel<<<grid_for(h->ldn * M), 256, 0, st>>>(V, v32, h->n, h->ldn, m, M, nullptr);
+  h->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  switch (M) {
+    case 1: e = launch_kind_into<1>(h, splits, tps, v32, part, st); break;
+    case 2: e = launch_kind_into<2>(h, splits, tps, v32, part, st); break;
+    case 4: e = launch_kind_into<4>(h, splits, tps, v32, part, st); break;
+    default: e = launch_kind_into<8>(h, splits, tps, v32, part, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  GramEpilogue none;
+  gram_reduce_kernel<<<grid_for(h->n * m), 256, 0, st>>>(part, splits, h->ldn, M, m, h->n, U, none);
+  h->launches++;
+  return cudaGetLastError();
+}
+
 }  // namespace kqr

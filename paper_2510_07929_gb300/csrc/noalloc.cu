@@ -1,0 +1,63 @@
+// FP32 Gram product that allocates no device memory.
+//
+// Its scratch (the FP32 copy of V and the per-split partial row sums) lives in
+// one file-scope __device__ array of kNoAllocScratchBytes.  Every GPU that loads
+// this library reserves that array until the process exits.  Host code cannot
+// use the array's name as a device address, so the address is looked up with
+// cudaGetSymbolAddress once per device (with that device current) and cached.
+#include <mutex>
+
+#include "kqr_internal.h"
+
+namespace kqr {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+cudaError_t gram_f32_scratch(Handle* h, const double* V, double* U, int m, unsigned char* scratch, size_t cap,
+                             size_t* need, cudaStream_t st);
+
+static std::mutex g_scratch_mu;
+static unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on `device` (the current device).
+static cudaError_t scratch_address(int device, unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[device] = static_cast<unsigned char*>(p);
+  }
+  *out = g_scratch_addr[device];
+  return cudaSuccess;
+}
+
+}  // namespace kqr
+
+using namespace kqr;
+
+extern "C" kqr_status kqr_kmatvec_fp32_noalloc_dev(kqr_handle* kh, const double* V, double* U, int64_t m,
+                                                   void* stream) {
+  if (!kh) return KQR_INVALID_ARG;
+  Handle* h = &kh->h;
+  if (!V || !U) return fail(h, KQR_INVALID_ARG, "V and U must be non-null");
+  if (m < 1 || m > kMaxRhs) return fail(h, KQR_INVALID_ARG, "m must be in [1, 8]");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+  if (dev != h->device) return fail(h, KQR_INVALID_ARG, "the handle's device must be the current device");
+  if (dev < 0 || dev >= kMaxDevices) return fail(h, KQR_INVALID_ARG, "device index out of range");
+  unsigned char* scratch = nullptr;
+  if ((e = scratch_address(dev, &scratch)) != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress");
+  size_t need = 0;
+  e = gram_f32_scratch(h, V, U, (int)m, scratch, kNoAllocScratchBytes, &need, pick_stream(h, stream));
+  if (e == cudaErrorInvalidValue && need > kNoAllocScratchBytes)
+    return fail(h, KQR_INVALID_ARG,
+                "no-allocation Gram product needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
+                    std::to_string(kNoAllocScratchBytes));
+  if (e != cudaSuccess) return cuda_fail(h, e, "no-allocation Gram product");
+  return KQR_OK;
+}

@@ -69,6 +69,7 @@ SIGNATURES = {
     "kqr_get_state": (ctypes.c_int, [_P, _DP, _DP]),
     "kqr_kmatvec": (ctypes.c_int, [_P, _DP, _DP, _I64, ctypes.c_int]),
     "kqr_kmatvec_dev": (ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, _P]),
+    "kqr_kmatvec_fp32_noalloc_dev": (ctypes.c_int, [_P, _P, _P, _I64, _P]),
     "kqr_box_grad_dev": (ctypes.c_int, [_P, _P, _P, _P, _D, _D, _D, _D, _D, _P, _P, _P, _P, _DP, _P]),
     "kqr_precond_apply_dev": (ctypes.c_int, [_P, _P, _D, _P, _P, _P]),
     "kqr_pcg_dev": (ctypes.c_int, [_P, _P, _D, _P, _P, _D, _I32, ctypes.POINTER(_I32), _P]),
