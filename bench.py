@@ -269,21 +269,25 @@ def run_ours(args):
 
     last = infos[-1]
     n, p = wl.n, wl.p
-    entries = float(n) * float(n)
+    # the single-vector products form each off-diagonal tile once: n(n+1)/2 entries,
+    # each with two FFMAs (row and column sums)
+    entries = float(n) * float(n + 1) / 2.0
+    sym_extra = 1
     roofline = None
     if n32 > 0:
         avg_s = ms32 / n32 / 1e3
         if wl.kind == "laplacian":
-            ops_per_entry = 2 * p + 1           # |x - x'| accumulate: FADD + FADD|.| per feature; FFMA with v
-            flops_per_entry = 3 * p + 4         # sub, abs, add per feature; scale, exp, multiply, add
+            ops_per_entry = 2 * p + 1 + sym_extra   # FADD + FADD|.| per feature; FFMA with v_j (and v_i)
+            flops_per_entry = 3 * p + 4             # sub, abs, add per feature; scale, exp, multiply, add
         else:
-            ops_per_entry = p + 3
+            ops_per_entry = p + 3 + sym_extra
             flops_per_entry = 2 * p + 5
         peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # Top/s, FP32 pipe lane-ops
         achieved = entries * ops_per_entry / avg_s / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "gram_f32_kernel (FP32 Gram tiles)",
-                    "launches": n32, "avg_ms": ms32 / n32, "kv_tflops": entries * flops_per_entry / avg_s / 1e12,
+                    "traffic": None, "kernel": "gram_f32_sym_kernel (FP32 Gram tiles, symmetric)",
+                    "launches": n32, "avg_ms": ms32 / n32, "entries_per_launch": entries,
+                    "kv_tflops_effective": float(n) * n * flops_per_entry / avg_s / 1e12,
                     "peak_basis": "152 SM x 128 FP32 lanes x 2070 MHz (derived, not measured)"}
     hp = {"launches": nhp, "avg_ms": (mshp / nhp) if nhp else None}
 
@@ -298,6 +302,7 @@ def run_ours(args):
             "solve": {"kkt": max(kkts), "phase1_iters": last["phase1_iters"], "alm_iters": last["phase2_iters"],
                       "newton_steps": last["newton_steps"], "cg_iters": last["pcg_iters"],
                       "gram_fp32": last["matvecs_fp32"], "gram_high": last["matvecs_high"], "rank": last["rank"],
+                      "core_builds": last["core_builds"],
                       "eta_gap": last["eta_gap"], "wall_s": t_wall, "setup_s": sum(setup_ms) / 1e3 / args.steps}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per_mv, nrows, dt = oracle_matvec_seconds(wl, rows=96 if n >= 100000 else min(n, 2000))

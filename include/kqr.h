@@ -67,10 +67,15 @@ typedef enum kqr_kernel {
  *   Laplacian: exact fixed-point L1 distances plus double-float exp and sums on
  *   the FP32/INT32 pipes; RBF: FP64).  Used for gradients and KKT residuals.
  * KQR_PREC_FP32: FP32 entries and FP32 partial sums, about 1e-6 relative per
- *   entry.  Used inside CG. */
+ *   entry.  Used inside CG.  RBF: the cross term x_i . x_j runs on the tcgen05
+ *   tensor cores as three TF32 products (hi.hi + hi.lo + lo.hi of a TF32 split
+ *   of X), unless options.rbf_tensor_cores = 0 (FP32 CUDA cores).
+ * KQR_PREC_TF32: RBF only; one TF32 product on the tensor cores (about 2^-11
+ *   relative error in the exponent's cross term). */
 typedef enum kqr_precision {
   KQR_PREC_HIGH = 0,
-  KQR_PREC_FP32 = 1
+  KQR_PREC_FP32 = 1,
+  KQR_PREC_TF32 = 2
 } kqr_precision;
 
 /* Preconditioner for the linear systems (2.1) and (3.1).
@@ -114,8 +119,14 @@ typedef struct kqr_options {
   int32_t ssn_maxit;             /* Newton steps per ALM subproblem */
   int32_t ls_maxit;              /* backtracking steps per Newton step */
   int32_t pcg_maxit;             /* CG iterations per linear system */
+  double core_reuse_rtol;        /* Newton steps keep the Woodbury core while the preconditioner's
+                                    diagonal moved by at most this relative amount (0: always rebuild) */
   double time_limit_s;           /* host wall-clock limit per solve; <= 0: none */
   int32_t phase1_only;           /* 1: stop after Phase I (for tests of Alg. 1) */
+  int32_t symmetric_gram;        /* 1: single-vector products (FP32, and FP64-class Laplacian) form each off-diagonal tile once and
+                                    use it for both K_IJ v_J and K_IJ^T v_I (n(n+1)/2 entries; summation
+                                    order not fixed); 0: every entry formed (deterministic) */
+  int32_t rbf_tensor_cores;      /* 1: RBF FP32 products on tcgen05 (three TF32 terms); 0: FP32 CUDA cores */
   int32_t verbose;               /* 1: one line per outer iteration on stderr */
 } kqr_options;
 
@@ -124,6 +135,7 @@ typedef struct kqr_info {
   int32_t phase1_iters, phase2_iters, newton_steps, pcg_iters;
   int32_t matvecs_fp32, matvecs_high;  /* Gram products by arithmetic, each counted once per RHS */
   int32_t rank;                        /* preconditioner rank r */
+  int32_t core_builds;                 /* Woodbury cores built (the rest of the systems reused one) */
   double eta_p, eta_d, eta_c, eta_kkt, eta_gap, obj_p, obj_d;
   double sigma_final;
   double seconds;                      /* wall-clock of the solve */

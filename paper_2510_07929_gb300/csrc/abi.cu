@@ -140,10 +140,24 @@ static bool make_tmap(CUtensorMap* tm, void* base, CUtensorMapDataType dt, int64
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map over a row-major [ldn][Kp] FP32 array, box 32 x 128 (128 bytes x 128 rows),
+// 128-byte swizzle: the canonical K-major operand layout of tcgen05.mma.
+bool make_tmap_rowmajor_sw128(CUtensorMap* tm, void* base, int64_t ldn, int Kp) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)ldn};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+  cuuint32_t box[2] = {32, 128};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 static void free_all(Handle* h) {
   void* bufs[] = {h->xs32, h->nrm32, h->hq, h->hl, h->exp_table, h->xc64, h->y, h->F32, h->dres, h->core, h->tvec,
                   h->Linv, h->part, h->v32, h->vec_pool, h->scal, h->red_counter, h->red_part, h->err_flag,
-                  h->st_alpha, h->st_v, h->st_z};
+                  h->st_alpha, h->st_v, h->st_z, h->sym_units, h->tc_hi, h->tc_lo};
   for (void* b : bufs) dev_free(h, b);
   if (h->scal_host) cudaFreeHost(h->scal_host);
   for (int k = 0; k < 2; ++k) {
@@ -311,8 +325,11 @@ void kqr_default_options(kqr_options* o) {
   o->ssn_maxit = 50;
   o->ls_maxit = 40;
   o->pcg_maxit = 1000;
+  o->core_reuse_rtol = 1e-2;
   o->time_limit_s = 0.0;
   o->phase1_only = 0;
+  o->symmetric_gram = 1;
+  o->rbf_tensor_cores = 1;
   o->verbose = 0;
 }
 
@@ -423,7 +440,10 @@ kqr_status kqr_kmatvec_dev(kqr_handle* kh, const double* V, double* U, int64_t m
   cudaError_t e;
   if (prec == KQR_PREC_FP32) e = gram_f32(h, V, U, (int)m, nullptr, st);
   else if (prec == KQR_PREC_HIGH) e = gram_high(h, V, U, (int)m, st);
-  else return fail(h, KQR_INVALID_ARG, "unknown precision");
+  else if (prec == KQR_PREC_TF32) {
+    if (h->kind != KQR_RBF) return fail(h, KQR_INVALID_ARG, "KQR_PREC_TF32 applies to the RBF kernel only");
+    e = gram_rbf_tc(h, V, U, (int)m, false, nullptr, st);
+  } else return fail(h, KQR_INVALID_ARG, "unknown precision");
   if (e != cudaSuccess) return cuda_fail(h, e, "Gram product");
   return KQR_OK;
 }

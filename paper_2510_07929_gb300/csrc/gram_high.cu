@@ -325,6 +325,7 @@ cudaError_t gram_column(Handle* h, int64_t s, double* col, cudaStream_t st) {
 }
 
 cudaError_t gram_high(Handle* h, const double* V, double* U, int m, cudaStream_t st) {
+  if (m == 1 && h->kind == KQR_LAPLACIAN && h->opt.symmetric_gram) return gram_high_sym(h, V, U, st);
   const int row_tiles = (int)(h->ldn / kTile), col_tiles = row_tiles;
   const int target = 8 * h->num_sms;
   int s = (target + row_tiles - 1) / row_tiles;

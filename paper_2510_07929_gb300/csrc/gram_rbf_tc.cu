@@ -1,0 +1,380 @@
+// RBF Gram product U = K V with the cross term on the tcgen05 tensor cores.
+//
+// K_ij = exp2(2 xs_i . xs_j - |xs_i|^2 - |xs_j|^2) (Sec. 1 RBF kernel, with
+// xs = sqrt(gamma log2 e)(x - mean)).  The 128 x 128 tile of dot products
+// xs_I xs_J^T is a dense contraction over p: it runs as tcgen05.mma kind::tf32
+// (M = N = 128, K = 8 per instruction) from shared-memory tiles that TMA loads
+// with the 128-byte swizzle, into an FP32 accumulator in tensor memory (two
+// 128-column buffers, so the MMAs of tile q overlap the epilogue of tile q-1).
+// FP32 accuracy comes from splitting xs = hi + lo into TF32 parts and summing
+// hi.hi + hi.lo + lo.hi (the lo.lo term is below FP32 rounding); one term
+// (hi.hi) gives the TF32 product.
+//
+// One CTA = 4 warps = 128 threads; thread t owns TMEM lane t = row t of the
+// tile, reads its 128 accumulators with tcgen05.ld and accumulates
+// exp2(...) v_j in registers, so rows need no cross-thread reduction.  Thread 0
+// issues the TMA copies and the MMAs.  Column tiles are split over
+// gridDim.y; per-split row sums are added in FP64 by a second kernel.
+// Every mbarrier wait is bounded; on a timeout the CTA records the error,
+// stops issuing work and frees its tensor memory.
+#include "kqr_internal.h"
+#include "ptx.cuh"
+
+namespace kqr {
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] B[smem]^T, tf32 inputs, FP32 accumulate.
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand in the canonical 128-byte
+// swizzled layout (8-row groups 1024 bytes apart), tcgen05 version bits 0b001.
+__device__ __forceinline__ uint64_t umma_desc_sw128(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // fixed 0b001
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+
+constexpr uint32_t kAtomBytes = 128 * 128;   // 128 rows x 128 bytes (32 tf32 of K)
+
+template <int M, int NTERMS>
+__global__ void __launch_bounds__(128, 1)
+    gram_rbf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+                       const float* __restrict__ nrm, const float* __restrict__ v32, float* __restrict__ part,
+                       int ksteps, int katoms, int ldn, int tiles_per_split, int col_tiles, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  const uint32_t tb = (uint32_t)katoms * kAtomBytes;   // one operand tile
+  unsigned char* XIh = base;
+  unsigned char* XIl = XIh + tb;
+  unsigned char* XJh[2] = {XIl + tb, XIl + 3 * tb};
+  unsigned char* XJl[2] = {XIl + 2 * tb, XIl + 4 * tb};
+  float* s_nrm = reinterpret_cast<float*>(XIl + 5 * tb);   // [2][128]
+  float* s_v = s_nrm + 2 * 128;                             // [2][128 * M]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_v + 2 * 128 * M);  // 0: XI, 1-2: stages, 3-4: MMA buffers
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row0 = blockIdx.x * 128;
+  const int split = blockIdx.y;
+  const int jt0 = split * tiles_per_split;
+  const int jt1 = min(col_tiles, jt0 + tiles_per_split);
+  const int nt = jt1 - jt0;
+  const uint32_t load_bytes = (NTERMS == 3 ? 2u : 1u) * tb;
+
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 256);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto load_tile = [&](unsigned char* dh, unsigned char* dl, int row, uint64_t* bar) {
+    mbar_arrive_expect_tx(bar, load_bytes);
+    for (int a = 0; a < katoms; ++a) {
+      tma_load_2d(dh + a * kAtomBytes, &tm_hi, a * 32, row, bar);
+      if (NTERMS == 3) tma_load_2d(dl + a * kAtomBytes, &tm_lo, a * 32, row, bar);
+    }
+  };
+  if (tid == 0) {
+    load_tile(XIh, XIl, row0, &bars[0]);
+    if (nt > 0) load_tile(XJh[0], XJl[0], jt0 * 128, &bars[1]);
+    if (nt > 1) load_tile(XJh[1], XJl[1], (jt0 + 1) * 128, &bars[2]);
+  }
+  const float ni = nrm[row0 + tid];
+  float racc[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) racc[c] = 0.f;
+  // kind::tf32, FP32 accumulate, A and B K-major, N = 128, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+  for (int q = 0; q <= nt; ++q) {
+    if (q < nt) {
+      const int col = (jt0 + q) * 128 + tid;
+      s_nrm[(q & 1) * 128 + tid] = __ldg(nrm + col);
+#pragma unroll
+      for (int c = 0; c < M; ++c) s_v[(q & 1) * 128 * M + tid * M + c] = __ldg(v32 + (size_t)col * M + c);
+    }
+    if (q < nt && tid == 0) {
+      bool ok = true;
+      if (q == 0) ok = mbar_wait_bounded(&bars[0], 0, err);
+      if (ok) ok = mbar_wait_bounded(&bars[1 + (q & 1)], (uint32_t)((q >> 1) & 1), err);
+      if (ok) {
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)((q & 1) * 128);
+        const unsigned char* bh = XJh[q & 1];
+        const unsigned char* bl = XJl[q & 1];
+        for (int k = 0; k < ksteps; ++k) {
+          const uint32_t off = (uint32_t)(k >> 2) * kAtomBytes + (uint32_t)(k & 3) * 32u;
+          umma_tf32(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bh + off), idesc, k > 0 ? 1u : 0u);
+          if (NTERMS == 3) {
+            umma_tf32(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bl + off), idesc, 1u);
+            umma_tf32(d, umma_desc_sw128(XIl + off), umma_desc_sw128(bh + off), idesc, 1u);
+          }
+        }
+        umma_commit(&bars[3 + (q & 1)]);
+      } else {
+        *abort_flag = 1;
+      }
+    }
+    if (q >= 1) {
+      const int pq = q - 1;
+      const int b = pq & 1;
+      if (mbar_wait_bounded(&bars[3 + b], (uint32_t)((pq >> 1) & 1), err)) {
+        tc_fence_after();
+        const uint32_t tbase = tmem + (uint32_t)(b * 128) + ((uint32_t)(warp * 32) << 16);
+        const float* nj = s_nrm + b * 128;
+        const float* vj = s_v + b * 128 * M;
+#pragma unroll 1
+        for (int c4 = 0; c4 < 4; ++c4) {
+          float g[32];
+          tmem_ld32(tbase + (uint32_t)(c4 * 32), g);
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const int col = c4 * 32 + jj;
+            const float e = ex2_approx(fmaf(2.f, g[jj], -(ni + nj[col])));
+#pragma unroll
+            for (int c = 0; c < M; ++c) racc[c] = fmaf(e, vj[col * M + c], racc[c]);
+          }
+        }
+      } else {
+        *abort_flag = 1;
+      }
+      tc_fence_before();
+    }
+    __syncthreads();
+    if (*abort_flag) break;
+    // Stage (q + 1) & 1 held tile q - 1, whose MMAs completed above: refill it with tile q + 1.
+    if (tid == 0 && q >= 1 && q + 1 < nt) load_tile(XJh[(q + 1) & 1], XJl[(q + 1) & 1], (jt0 + q + 1) * 128, &bars[1 + ((q + 1) & 1)]);
+  }
+#pragma unroll
+  for (int c = 0; c < M; ++c) part[((size_t)split * ldn + row0 + tid) * M + c] = racc[c];
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// xs32 (feature-major [p][ldn]) -> row-major TF32 parts [ldn][Kp], zero padded.
+__global__ void tf32_split_kernel(const float* __restrict__ xs32, int64_t ldn, int p, int Kp, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ldn * Kp; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / Kp;
+    const int k = (int)(e % Kp);
+    const float x = k < p ? xs32[(size_t)k * ldn + i] : 0.f;
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float r = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+    hi[e] = __uint_as_float(h);
+    lo[e] = __uint_as_float(l);
+  }
+}
+
+__global__ void tc_to_f32_kernel(const double* __restrict__ V, float* __restrict__ v32, int64_t n, int64_t ldn, int m,
+                                 int M, double* __restrict__ sum_out) {
+  double s = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < ldn * M;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / M;
+    const int c = (int)(idx % M);
+    const double x = (i < n && c < m) ? V[i * m + c] : 0.0;
+    v32[idx] = (float)x;
+    if (c == 0) s += x;
+  }
+  if (sum_out) {
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+      atomicAdd(sum_out, t);
+    }
+  }
+}
+
+// out = sum of split partials (+ gam sum_p + L p for the CG operator); dot_out += p . out.
+__global__ void tc_reduce_kernel(const float* __restrict__ part, int splits, int64_t ldn, int M, int m, int64_t n,
+                                 double* __restrict__ out, GramEpilogue ep) {
+  double dot = 0.0;
+  const double sump = ep.sum_p ? *ep.sum_p : 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / m;
+    const int c = (int)(idx % m);
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp) s += (double)part[((size_t)sp * ldn + row) * M + c];
+    if (ep.raw_out) ep.raw_out[idx] = s;
+    if (ep.L) s += ep.gam * sump + ep.L[row] * ep.pvec[row];
+    out[idx] = s;
+    if (ep.dot_out) dot += ep.pvec[row] * s;
+  }
+  if (ep.dot_out) {
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = dot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+      atomicAdd(ep.dot_out, t);
+    }
+  }
+}
+
+static size_t tc_smem(int katoms, int M) {
+  return 1024 + (size_t)6 * katoms * kAtomBytes + (2 * 128 + 2 * 128 * (size_t)M) * sizeof(float) + 5 * 8 + 16;
+}
+
+bool make_tmap_rowmajor_sw128(CUtensorMap* tm, void* base, int64_t ldn, int Kp);
+
+// Prepares the TF32 row-major copies and their tensor maps (once per problem).
+cudaError_t rbf_tc_prepare(Handle* h) {
+  if (h->tc_hi) return cudaSuccess;
+  const int Kp = h->p <= 32 ? 32 : 64;
+  const size_t bytes = (size_t)h->ldn * Kp * sizeof(float);
+  h->tc_hi = (float*)dev_alloc(h, bytes);
+  h->tc_lo = (float*)dev_alloc(h, bytes);
+  if (!h->tc_hi || !h->tc_lo) return cudaErrorMemoryAllocation;
+  h->tc_Kp = Kp;
+  tf32_split_kernel<<<grid_for(h->ldn * Kp), 256, 0, h->stream>>>(h->xs32, h->ldn, (int)h->p, Kp, h->tc_hi, h->tc_lo);
+  h->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (!make_tmap_rowmajor_sw128(&h->tm_tc_hi, h->tc_hi, h->ldn, Kp) ||
+      !make_tmap_rowmajor_sw128(&h->tm_tc_lo, h->tc_lo, h->ldn, Kp))
+    return cudaErrorInvalidValue;
+  return cudaStreamSynchronize(h->stream);
+}
+
+template <int M, int NT>
+static cudaError_t launch_tc(Handle* h, int splits, int tps, int ksteps, cudaStream_t st) {
+  const int katoms = h->tc_Kp / 32;
+  const size_t smem = tc_smem(katoms, M);
+  auto kern = gram_rbf_tc_kernel<M, NT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int row_tiles = (int)(h->ldn / kTile);
+  prof_mark(h, 0, true, st);
+  kern<<<dim3(row_tiles, splits), 128, smem, st>>>(h->tm_tc_hi, h->tm_tc_lo, h->nrm32, h->v32, h->part, ksteps,
+                                                   katoms, (int)h->ldn, tps, row_tiles, h->err_flag);
+  prof_mark(h, 0, false, st);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+// U = K V on the tensor cores; three_terms selects FP32 (hi.hi + hi.lo + lo.hi) or TF32 (hi.hi).
+cudaError_t gram_rbf_tc(Handle* h, const double* V, double* U, int m, bool three_terms, const GramEpilogue* ep,
+                        cudaStream_t st) {
+  cudaError_t e = rbf_tc_prepare(h);
+  if (e != cudaSuccess) return e;
+  const int M = m <= 1 ? 1 : (m <= 2 ? 2 : (m <= 4 ? 4 : 8));
+  const int row_tiles = (int)(h->ldn / kTile), col_tiles = row_tiles;
+  const int katoms = h->tc_Kp / 32;
+  const int resident = tc_smem(katoms, M) * 2 <= 228 * 1024 ? 2 : 1;
+  const int target = 8 * resident * h->num_sms;
+  int s = (target + row_tiles - 1) / row_tiles;
+  if (s < 1) s = 1;
+  if (s > col_tiles) s = col_tiles;
+  const int tps = (col_tiles + s - 1) / s;
+  const int splits = (col_tiles + tps - 1) / tps;
+  const size_t vb = (size_t)h->ldn * M * sizeof(float) * 2;
+  if (h->v32_cap < vb) {
+    dev_free(h, h->v32);
+    h->v32 = (float*)dev_alloc(h, vb);
+    h->v32_cap = h->v32 ? vb : 0;
+    if (!h->v32) return cudaErrorMemoryAllocation;
+  }
+  const size_t pb = (size_t)splits * h->ldn * M * sizeof(float);
+  if (h->part_cap < pb) {
+    dev_free(h, h->part);
+    h->part = (float*)dev_alloc(h, pb);
+    h->part_cap = h->part ? pb : 0;
+    if (!h->part) return cudaErrorMemoryAllocation;
+  }
+  GramEpilogue none;
+  const GramEpilogue& g = ep ? *ep : none;
+  double* sum_out = g.sum_p ? const_cast<double*>(g.sum_p) : nullptr;
+  if (sum_out && (e = cudaMemsetAsync(sum_out, 0, sizeof(double), st)) != cudaSuccess) return e;
+  tc_to_f32_kernel<<<grid_for(h->ldn * M), 256, 0, st>>>(V, h->v32, h->n, h->ldn, m, M, sum_out);
+  h->launches++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int ksteps = (int)((h->p + 7) / 8);
+  if (three_terms) {
+    switch (M) {
+      case 1: e = launch_tc<1, 3>(h, splits, tps, ksteps, st); break;
+      case 2: e = launch_tc<2, 3>(h, splits, tps, ksteps, st); break;
+      case 4: e = launch_tc<4, 3>(h, splits, tps, ksteps, st); break;
+      default: e = launch_tc<8, 3>(h, splits, tps, ksteps, st); break;
+    }
+  } else {
+    switch (M) {
+      case 1: e = launch_tc<1, 1>(h, splits, tps, ksteps, st); break;
+      case 2: e = launch_tc<2, 1>(h, splits, tps, ksteps, st); break;
+      case 4: e = launch_tc<4, 1>(h, splits, tps, ksteps, st); break;
+      default: e = launch_tc<8, 1>(h, splits, tps, ksteps, st); break;
+    }
+  }
+  if (e != cudaSuccess) return e;
+  if (g.dot_out && (e = cudaMemsetAsync(g.dot_out, 0, sizeof(double), st)) != cudaSuccess) return e;
+  tc_reduce_kernel<<<grid_for(h->n * m), 256, 0, st>>>(h->part, splits, h->ldn, M, m, h->n, U, g);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace kqr

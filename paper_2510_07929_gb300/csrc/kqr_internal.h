@@ -50,7 +50,15 @@ struct GramEpilogue {
 };
 
 cudaError_t gram_f32(Handle* h, const double* V, double* U, int m, const GramEpilogue* ep, cudaStream_t st);
+// RBF product with the cross term on tcgen05 (gram_rbf_tc.cu): FP32 accuracy
+// (three TF32 terms) or TF32 (one term); ep as for gram_f32.
+cudaError_t gram_rbf_tc(Handle* h, const double* V, double* U, int m, bool three_terms, const GramEpilogue* ep,
+                        cudaStream_t st);
+// m = 1 product with each off-diagonal tile formed once (gram_f32_sym.cu).
+cudaError_t gram_f32_sym(Handle* h, const double* V, double* U, const GramEpilogue* ep, cudaStream_t st);
 cudaError_t gram_high(Handle* h, const double* V, double* U, int m, cudaStream_t st);
+// Laplacian m = 1 FP64-class product with each off-diagonal tile formed once (gram_high_sym.cu).
+cudaError_t gram_high_sym(Handle* h, const double* V, double* U, cudaStream_t st);
 // Column s of K in FP64 (RPCholesky).
 cudaError_t gram_column(Handle* h, int64_t s, double* col, cudaStream_t st);
 
@@ -92,6 +100,19 @@ struct Handle {
   double* tvec = nullptr;             // r + 1
   double* Linv = nullptr;             // n
   bool core_valid = false;
+  double core_gam = 0.0;              // gam the current core was built for
+  kqr_precond core_kind = KQR_PRECOND_NYSTROM_DIAG;
+  int64_t core_builds = 0, core_reuses = 0;
+
+  // RBF tensor-core path: row-major TF32 parts [ldn][tc_Kp] and their swizzled tensor maps.
+  float* tc_hi = nullptr;
+  float* tc_lo = nullptr;
+  int tc_Kp = 0;
+  CUtensorMap tm_tc_hi{}, tm_tc_lo{};
+
+  // Symmetric Gram product: work-unit table (row tile, first and end column tile).
+  int4* sym_units = nullptr;
+  int sym_nunits = 0, sym_T = 0;
 
   // Gram-product scratch.
   float* part = nullptr;  size_t part_cap = 0;      // per-split partial sums (bytes)
@@ -167,6 +188,10 @@ cudaError_t fill_L(Handle* h, double* L, double base, const double* dres, int64_
 
 // ---- preconditioner (woodbury.cu, rpchol.cu) -------------------------------------
 kqr_status precond_build(Handle* h, const double* Ldiag, double gam, cudaStream_t st);
+// As precond_build, but keeps the current core when it was built for the same gam
+// and max_i |Lpre_i - Lcore_i| / Lcore_i <= rtol (the preconditioner stays SPD; only
+// its distance to the exact P changes).  Lcore_i = 1 / Linv_i.
+kqr_status precond_update(Handle* h, const double* Lpre, double gam, double rtol, cudaStream_t st);
 cudaError_t precond_apply(Handle* h, const double* Ldiag, const double* r, double* out, double* rz_out,
                           cudaStream_t st);
 kqr_status rpcholesky_setup(Handle* h, const double* uniforms);

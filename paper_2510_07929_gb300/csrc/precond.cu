@@ -15,6 +15,7 @@
 // with the (r+1)^2 core built in FP64, Cholesky-factorised and inverted on the
 // device; each apply is two skinny FP64 products with the FP32 factor.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "kqr_internal.h"
@@ -259,8 +260,41 @@ __global__ void ident_dot_kernel(const double* __restrict__ rv, double* __restri
   }
 }
 
+// max_i |Lpre_i Linv_i - 1| (relative change of the diagonal since the last build)
+__global__ void rel_change_kernel(const double* __restrict__ Lpre, const double* __restrict__ Linv, int64_t n,
+                                  unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  GRID_LOOP(i, n) m = fmax(m, fabs(Lpre[i] * Linv[i] - 1.0));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));  // m >= 0: bit order = value order
+}
+
+kqr_status precond_update(Handle* h, const double* Lpre, double gam, double rtol, cudaStream_t st) {
+  if (h->core_valid && h->core_gam == gam && h->core_kind == h->opt.precond && h->opt.precond != KQR_PRECOND_NONE) {
+    unsigned long long* slot = reinterpret_cast<unsigned long long*>(h->scal + S_COUNT - 2);
+    cudaError_t e = cudaMemsetAsync(slot, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "core reuse check");
+    rel_change_kernel<<<grid_for(h->n), 256, 0, st>>>(Lpre, h->Linv, h->n, slot);
+    h->launches++;
+    unsigned long long bits = 0;
+    if ((e = cudaMemcpyAsync(&bits, slot, sizeof(bits), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return cuda_fail(h, e, "core reuse check");
+    double change;
+    std::memcpy(&change, &bits, sizeof(change));
+    if (change <= rtol) {
+      h->core_reuses++;
+      return KQR_OK;
+    }
+  }
+  return precond_build(h, Lpre, gam, st);
+}
+
 kqr_status precond_build(Handle* h, const double* Lpre, double gam, cudaStream_t st) {
   h->core_valid = false;
+  h->core_gam = gam;
+  h->core_kind = h->opt.precond;
+  h->core_builds++;
   if (h->opt.precond == KQR_PRECOND_NONE) {
     h->core_valid = true;
     return KQR_OK;

@@ -178,6 +178,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
   const double* dres = (o.precond == KQR_PRECOND_NYSTROM_DIAG) ? h->dres : nullptr;
   kqr_info inf{};
   inf.rank = h->r;
+  const int64_t builds0 = h->core_builds;
   double res[7] = {0, 0, 0, 0, 0, 0, 0};
   CK(vec_fill(h, alpha, 0.0, n, st));
   CK(vec_fill(h, v, 0.0, n, st));
@@ -271,7 +272,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
         make_L_kernel<<<grid_for(n), 256, 0, st>>>(L, Lpre, S, lam * sigma, lam * eps, dres, n);
         h->launches++;
         CK(cudaGetLastError());
-        KS(precond_build(h, Lpre, lam * sigma, st));
+        KS(precond_update(h, Lpre, lam * sigma, o.core_reuse_rtol, st));
         CK(scale_vec(h, b, g, -lam, n, st));
         const double ptol = lam * std::fmin(o.eta_bar, std::pow(ng, 1.0 + o.iota));
         int its = 0;
@@ -347,6 +348,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
   inf.obj_p = res[5];
   inf.obj_d = res[6];
   inf.sigma_final = sigma;
+  inf.core_builds = (int32_t)(h->core_builds - builds0);
   inf.seconds = now_s() - t_start;
   if (info) *info = inf;
   if (status != KQR_OK) return status;

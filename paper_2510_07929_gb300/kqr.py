@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libkqr.so")
 
 RBF, LAPLACIAN = 0, 1
-PREC_HIGH, PREC_FP32 = 0, 1
+PREC_HIGH, PREC_FP32, PREC_TF32 = 0, 1, 2
 PRECOND_NYSTROM_DIAG, PRECOND_PAPER, PRECOND_NONE = 0, 1, 2
 KIND = {"rbf": RBF, "laplacian": LAPLACIAN}
 
@@ -37,7 +37,9 @@ class Options(ctypes.Structure):
         ("eta_bar", ctypes.c_double), ("iota", ctypes.c_double), ("mu", ctypes.c_double), ("r_ls", ctypes.c_double),
         ("tau1", ctypes.c_double), ("tau2", ctypes.c_double),
         ("ssn_maxit", ctypes.c_int32), ("ls_maxit", ctypes.c_int32), ("pcg_maxit", ctypes.c_int32),
-        ("time_limit_s", ctypes.c_double), ("phase1_only", ctypes.c_int32), ("verbose", ctypes.c_int32),
+        ("core_reuse_rtol", ctypes.c_double),
+        ("time_limit_s", ctypes.c_double), ("phase1_only", ctypes.c_int32),
+        ("symmetric_gram", ctypes.c_int32), ("rbf_tensor_cores", ctypes.c_int32), ("verbose", ctypes.c_int32),
     ]
 
 
@@ -45,7 +47,7 @@ class Info(ctypes.Structure):
     _fields_ = [
         ("phase1_iters", ctypes.c_int32), ("phase2_iters", ctypes.c_int32), ("newton_steps", ctypes.c_int32),
         ("pcg_iters", ctypes.c_int32), ("matvecs_fp32", ctypes.c_int32), ("matvecs_high", ctypes.c_int32),
-        ("rank", ctypes.c_int32),
+        ("rank", ctypes.c_int32), ("core_builds", ctypes.c_int32),
         ("eta_p", ctypes.c_double), ("eta_d", ctypes.c_double), ("eta_c", ctypes.c_double),
         ("eta_kkt", ctypes.c_double), ("eta_gap", ctypes.c_double), ("obj_p", ctypes.c_double),
         ("obj_d", ctypes.c_double), ("sigma_final", ctypes.c_double), ("seconds", ctypes.c_double),

@@ -39,10 +39,19 @@ GRAM_CASES = [("rbf", 2, 1), ("laplacian", 2, 1), ("rbf", 129, 3), ("laplacian",
               ("laplacian", 700, 64), ("rbf", 257, 64)]
 
 
+PATHS = {"sym_tc": dict(symmetric_gram=1, rbf_tensor_cores=1), "plain_tc": dict(symmetric_gram=0, rbf_tensor_cores=1),
+         "sym_cuda": dict(symmetric_gram=1, rbf_tensor_cores=0), "plain_cuda": dict(symmetric_gram=0, rbf_tensor_cores=0)}
+
+
+@pytest.mark.parametrize("path", list(PATHS))
 @pytest.mark.parametrize("kind,n,p", GRAM_CASES)
-def test_gram_products_match_oracle(K_, kind, n, p):
+def test_gram_products_match_oracle(K_, kind, n, p, path):
+    """Every Gram-product path: symmetric or plain tiles; RBF cross term on
+    tcgen05 (three TF32 terms) or on FP32 CUDA cores."""
+    if kind == "laplacian" and path.endswith("_cuda"):
+        pytest.skip("the tensor-core switch applies to the RBF kernel only")
     wl = _data(kind, n, p)
-    with K_.Problem(wl.X, wl.y, kind, wl.gamma) as prob:
+    with K_.Problem(wl.X, wl.y, kind, wl.gamma, **PATHS[path]) as prob:
         for m in (1, 3, 8):
             V = W.random_vectors(n, m, seed=m)
             ref = O.kmatvec(wl.X, V, kind, wl.gamma)
@@ -52,6 +61,29 @@ def test_gram_products_match_oracle(K_, kind, n, p):
             uhp = prob.kmatvec(V, K_.PREC_HIGH)
             err = np.abs(uhp - ref) / absref
             assert np.max(err) <= 1e-12, (m, np.max(err))
+
+
+@pytest.mark.parametrize("n,p", [(3001, 20), (1000, 10), (515, 50)])
+def test_tf32_gram_error_is_bounded(K_, n, p):
+    """KQR_PREC_TF32 (one TF32 tensor-core product for the cross term): the
+    exponent's cross term has relative error ~2^-11, so entries err by about
+    2^-11 * 2 |xs_i||xs_j|; check the product against that bound and that the
+    FP32 form is far more accurate."""
+    wl = _data("rbf", n, p)
+    v = W.random_vectors(n, seed=3)
+    ref = O.kmatvec(wl.X, v, "rbf", wl.gamma)
+    absref = O.kmatvec(wl.X, np.abs(v), "rbf", wl.gamma)
+    Xc = wl.X - wl.X.mean(0)
+    s2 = wl.gamma / np.log(2.0) * np.max(np.sum(Xc * Xc, axis=1))   # max |xs|^2
+    with K_.Problem(wl.X, wl.y, "rbf", wl.gamma) as prob:
+        u_tf32 = prob.kmatvec(v, K_.PREC_TF32)
+        u_fp32 = prob.kmatvec(v, K_.PREC_FP32)
+    err_tf32 = np.max(np.abs(u_tf32 - ref) / absref)
+    err_fp32 = np.max(np.abs(u_fp32 - ref) / absref)
+    bound = 2.0 ** -10 * 2 * s2 * np.log(2.0) + 1e-5
+    assert err_tf32 <= bound, (err_tf32, bound)
+    assert err_fp32 <= 1e-5
+    assert err_fp32 < err_tf32
 
 
 def test_gram_device_entry_and_stream(K_):
