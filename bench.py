@@ -49,9 +49,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verbose", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "gram"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "gram", "precision", "path", "grad", "batch"],
                     help="gram: time --matvecs FP32 and FP64-class Gram products only (kernel profiling)")
     ap.add_argument("--matvecs", type=int, default=3)
+    ap.add_argument("--ncu-window", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--path-gamma", type=float, default=0.1)
+    ap.add_argument("--path-tau", type=float, default=0.5)
+    ap.add_argument("--path-lambdas", type=int, default=50)
+    ap.add_argument("--path-precond", type=int, default=0, help="0 Nystrom+diag, 1 paper, 2 none (NALM)")
+    ap.add_argument("--prec-taus", default="0.5", help="comma-separated tau values for --mode precision")
+    ap.add_argument("--time-limit", type=float, default=600.0, help="per-solve wall-clock limit (s) in the study modes")
     return ap.parse_args()
 
 
@@ -209,6 +217,8 @@ def run_ours(args):
     setup_ms = []
     kkts = []
     barrier()
+    if args.ncu_window:
+        torch.cuda.profiler.start()
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(float(len(step_ms)))              # L2 flush outside the step's events
@@ -228,6 +238,8 @@ def run_ours(args):
         infos.append(info)
     barrier()
     t_wall = time.perf_counter() - t_wall0
+    if args.ncu_window:
+        torch.cuda.profiler.stop()
     clk = clocks.stop()
     launches = prob.launches - launches0
     n32, ms32 = prob.profile_read(0)
@@ -347,8 +359,250 @@ def run_gram(args):
     return 0
 
 
+def run_precision(args):
+    """Mixed-precision comparison on the RBF workload (n = 50000, p = 20,
+    lambda = 1e-3): solve seconds to the same KKT tolerance with (a) FP32
+    CUDA-core Gram products, (b) FP32 products with the cross term on tcgen05
+    (three TF32 terms), (c) TF32 tensor-core products inside CG refined against
+    FP32 residuals.  One JSON line per run, then a summary line."""
+    import torch
+
+    from paper_2510_07929_gb300 import build, workloads as W
+
+    build.build()
+    from paper_2510_07929_gb300 import kqr
+
+    n = args.n or 50000
+    configs = {"fp32_cuda_cores": dict(rbf_tensor_cores=0), "fp32_tcgen05": dict(rbf_tensor_cores=1),
+               "tf32_tcgen05_refined": dict(rbf_tensor_cores=1, cg_tf32=1)}
+    taus = [float(t) for t in args.prec_taus.split(",")]
+    runs = []
+    for tau in taus:
+        wl = W.rbf_mid(n=n, tau=tau)
+        for name, cfg in configs.items():
+            with kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, rank0=args.rank0, time_limit_s=args.time_limit,
+                             **cfg) as prob:
+                if args.warmup > 0:
+                    prob.solve(wl.tau, wl.lam, args.tol, allow_not_converged=True)
+                torch.cuda.synchronize()
+                prob.profile(True)
+                t0 = time.perf_counter()
+                _, _, kkt, info = prob.solve(wl.tau, wl.lam, args.tol, allow_not_converged=True)
+                dt = time.perf_counter() - t0
+                n_cg, ms_cg = prob.profile_read(0)             # CG Gram products (FP32 or TF32 tiles)
+                n_hp, ms_hp = prob.profile_read(1)             # FP64-class products
+                prob.profile(False)
+            run = {"tau": tau, "config": name, "status": info["status"], "seconds": dt,
+                   "cg_gram_seconds": ms_cg / 1e3, "high_gram_seconds": ms_hp / 1e3, "kkt": kkt,
+                   "eta_gap": info["eta_gap"], "gram_fp32": info["matvecs_fp32"], "gram_tf32": info["matvecs_low"],
+                   "gram_high": info["matvecs_high"], "cg_iters": info["pcg_iters"],
+                   "newton_steps": info["newton_steps"], "cg_truncations": info["cg_truncations"]}
+            runs.append(run)
+            print(json.dumps(dict(mode="precision_run", n=n, **run)), flush=True)
+    out = {"mode": "precision", "workload": f"rbf_mid n={n} p=20 gamma=1/p lambda=1e-3 tol={args.tol:g}"}
+    for tau in taus:
+        for key in ("seconds", "cg_gram_seconds"):
+            r = {x["config"]: x[key] for x in runs if x["tau"] == tau}
+            out[f"speedup_{key}_tau{tau}"] = {
+                "tcgen05_fp32_vs_cuda_fp32": r["fp32_cuda_cores"] / r["fp32_tcgen05"],
+                "mixed_vs_cuda_fp32": r["fp32_cuda_cores"] / r["tf32_tcgen05_refined"],
+                "mixed_vs_tcgen05_fp32": r["fp32_tcgen05"] / r["tf32_tcgen05_refined"]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# Total seconds of a 50-lambda path in the paper's Table 1 (MATLAB, Intel Xeon Platinum
+# 8375C, 128 cores; RBF kernel, p = 2 generator of Sec. 4.1, tolerance 1e-8), keyed by
+# (n, gamma, tau).  Context only: another machine, language and tolerance handling.
+PAPER_TABLE1_S = {
+    (5000, 0.1, 0.1): 45, (5000, 0.1, 0.5): 34, (5000, 0.1, 0.9): 36,
+    (10000, 0.1, 0.1): 146, (10000, 0.1, 0.5): 152, (10000, 0.1, 0.9): 161,
+    (20000, 0.1, 0.1): 881, (20000, 0.1, 0.5): 863, (20000, 0.1, 0.9): 801,
+    (5000, 0.01, 0.1): 40, (5000, 0.01, 0.5): 35, (5000, 0.01, 0.9): 35,
+    (10000, 0.01, 0.1): 121, (10000, 0.01, 0.5): 132, (10000, 0.01, 0.9): 144,
+    (20000, 0.01, 0.1): 763, (20000, 0.01, 0.5): 763, (20000, 0.01, 0.9): 765,
+    (5000, 0.001, 0.1): 28, (5000, 0.001, 0.5): 29, (5000, 0.001, 0.9): 31,
+    (10000, 0.001, 0.1): 83, (10000, 0.001, 0.5): 97, (10000, 0.001, 0.9): 111,
+    (20000, 0.001, 0.1): 501, (20000, 0.001, 0.5): 512, (20000, 0.001, 0.9): 514,
+}
+
+
+def run_path(args):
+    """A 50-lambda regularisation path (lambda log-spaced in [1e-2, 1]) on the
+    paper's p = 2 generator (Sec. 4.1), RBF kernel, tolerance 1e-8 per solve,
+    one handle (the RPCholesky factor is built once, as in Sec. 3), no warm
+    start across lambda."""
+    import torch
+
+    from paper_2510_07929_gb300 import build, workloads as W
+
+    build.build()
+    from paper_2510_07929_gb300 import kqr
+
+    n = args.n or 5000
+    tol = 1e-8
+    wl = W.yuan2006(n=n, gamma=args.path_gamma, tau=args.path_tau)
+    lams = np.logspace(-2, 0, args.path_lambdas)
+    t0 = time.perf_counter()
+    prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, precond=args.path_precond, time_limit_s=args.time_limit)
+    t_setup = time.perf_counter() - t0
+    per, worst, unsolved, products = [], 0.0, 0, 0
+    for lam in lams:
+        t1 = time.perf_counter()
+        _, _, kkt, info = prob.solve(wl.tau, float(lam), tol, allow_not_converged=True)
+        torch.cuda.synchronize()
+        per.append(time.perf_counter() - t1)
+        worst = max(worst, max(kkt, info["eta_gap"]))
+        unsolved += int(info["status"] != kqr.OK)
+        products += info["matvecs_fp32"] + info["matvecs_high"]
+        print(f"lambda={lam:.4g} status={info['status']} kkt={kkt:.2e} gap={info['eta_gap']:.2e} s={per[-1]:.2f} "
+              f"cg={info['pcg_iters']} newton={info['newton_steps']} trunc={info['cg_truncations']}",
+              file=sys.stderr, flush=True)
+    prob.close()
+    total = t_setup + sum(per)
+    key = (n, args.path_gamma, args.path_tau)
+    out = {"mode": "path", "workload": f"yuan2006 n={n} p=2 rbf gamma={args.path_gamma:g} tau={args.path_tau:g}",
+           "lambdas": len(lams), "tol": tol, "precond": ["nystrom_diag", "paper", "none"][args.path_precond],
+           "total_s": total, "setup_s": t_setup, "median_solve_s": float(np.median(per)), "max_solve_s": max(per),
+           "worst_kkt_or_gap": worst, "not_converged": unsolved, "gram_products": products,
+           "paper_total_s": PAPER_TABLE1_S.get(key), "paper_hardware": "MATLAB, Xeon Platinum 8375C, 128 cores"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_grad(args):
+    """Held-out loss gradient on the n = 20000 (+ 5000 held-out) p = 16 RBF
+    workload (gamma = 1/16, lambda = 1e-2, tau = 0.5): seconds of the forward
+    solve and of kqr_heldout_grad, with a central-difference check of the
+    log-lambda and log-gamma derivatives from four more solves."""
+    import torch
+
+    from paper_2510_07929_gb300 import build, workloads as W
+
+    build.build()
+    from paper_2510_07929_gb300 import kqr
+
+    n = args.n or 20000
+    nh = max(1, n // 4)
+    tau, lam, tol = 0.5, 1e-2, 1e-8
+    tr = W.rbf_small(n=n, p=16, seed=0, tau=tau, lam=lam)
+    ho = W.rbf_small(n=nh, p=16, seed=1000, tau=tau, lam=lam)
+    gamma = 1.0 / 16
+
+    def fwd(gm, lm, grad=True):
+        with kqr.Problem(tr.X, tr.y, "rbf", gm) as prob:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, kkt, info = prob.solve(tau, lm, tol)
+            t1 = time.perf_counter()
+            res = prob.heldout_grad(ho.X, ho.y, want_dX=grad)
+            t2 = time.perf_counter()
+        return res, t1 - t0, t2 - t1, kkt, info
+
+    fwd(gamma, lam)                                   # warm-up (build, allocator)
+    (loss, dg, dl, dX), t_solve, t_grad, kkt, info = fwd(gamma, lam)
+    h = 1e-4
+    fl = [fwd(gamma, lam * np.exp(s * h), False)[0][0] for s in (1, -1)]
+    fg = [fwd(gamma * np.exp(s * h), lam, False)[0][0] for s in (1, -1)]
+    out = {"mode": "grad", "workload": f"rbf n={n} + {nh} held-out, p=16, gamma=1/16, lambda={lam:g}, tau={tau:g}",
+           "solve_s": t_solve, "grad_s": t_grad, "kkt": kkt, "loss": loss, "d_loglambda": dl, "d_loggamma": dg,
+           "dX_max_abs": float(np.abs(dX).max()),
+           "fd_d_loglambda": (fl[0] - fl[1]) / (2 * h), "fd_d_loggamma": (fg[0] - fg[1]) / (2 * h),
+           "fd_step_log": h}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def batch_workload(seed: int = 0):
+    """64 problems, n_b ~ U{1000..20000}, x ~ U[0,1]^8, RBF gamma = 1/8, and 64
+    right-hand sides per problem (one per (tau, lambda) pair of an 8 x 8 grid)."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(1000, 20001, size=64)
+    Xs = [rng.random((int(n), 8)) for n in sizes]
+    V = rng.standard_normal((int(sizes.sum()), 64))
+    return Xs, V
+
+
+def run_batch(args):
+    """Batched multi-RHS products U_b = K_b V_b on the tensor cores: seconds per
+    batched product (all 64 problems, 64 right-hand sides), TFLOP/s at 2p + 2m
+    = 144 tensor flops per Gram entry, against the measured bf16 dense peak
+    scaled by the nominal TF32/bf16 ratio (1.1 / 2.25)."""
+    import torch
+
+    from paper_2510_07929_gb300 import build
+
+    build.build()
+    from paper_2510_07929_gb300 import kqr
+
+    Xs, V = batch_workload()
+    sizes = [x.shape[0] for x in Xs]
+    entries = float(sum(n * n for n in sizes))
+    peaks = {}
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    peak = bf16 * 1.1 / 2.25
+    with kqr.Batch(Xs, 0.125) as bt:
+        stream = torch.cuda.Stream()
+        bt.set_stream(stream)
+        Vd = torch.tensor(V, device="cuda")
+        Ud = torch.empty_like(Vd)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        for _ in range(max(3, args.warmup)):
+            bt.kmatmul_dev(Vd, Ud)
+        torch.cuda.synchronize()
+        steps = max(args.steps, 10)
+        bt.profile(True)
+        times = []
+        clocks = ClockSampler(0)
+        clocks.start()
+        for k in range(steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bt.kmatmul_dev(Vd, Ud)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        clk = clocks.stop()
+        nk, ms_k = bt.profile_read()
+        bt.profile(False)
+        # e2e: host V in pinned memory, host U, copies inside the timed region
+        Vh = torch.empty(V.shape, dtype=torch.float64, pin_memory=True)
+        Vh.numpy()[:] = V
+        t0 = time.perf_counter()
+        U = bt.kmatmul(Vh.numpy())
+        e2e_s = time.perf_counter() - t0
+    ms = statistics.median(times)
+    kern_ms = ms_k / max(nk, 1)
+    flops = entries * (2 * 8 + 2 * 64)
+    out = {"mode": "batch", "workload": "64 RBF problems, n_b ~ U{1000..20000} (seed 0), p=8, gamma=1/8, m=64",
+           "sum_n": int(sum(sizes)), "entries": entries, "ms_per_product": ms, "kernel_ms": kern_ms,
+           "tflops": flops / (kern_ms * 1e-3) / 1e12,
+           "roofline": {"bound": "tensor", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": peak,
+                        "unit": "TFLOP/s", "frac": flops / (kern_ms * 1e-3) / 1e12 / peak,
+                        "peak_basis": "measured bf16 dense x 1.1/2.25 (nominal TF32/bf16)"},
+           "e2e_s": e2e_s, "clocks": clk, "u_checksum": float(np.abs(U).sum())}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "grad":
+        return run_grad(args)
+    if args.mode == "path":
+        return run_path(args)
+    if args.mode == "precision":
+        return run_precision(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "gram":

@@ -127,6 +127,8 @@ typedef struct kqr_options {
                                     use it for both K_IJ v_J and K_IJ^T v_I (n(n+1)/2 entries; summation
                                     order not fixed); 0: every entry formed (deterministic) */
   int32_t rbf_tensor_cores;      /* 1: RBF FP32 products on tcgen05 (three TF32 terms); 0: FP32 CUDA cores */
+  int32_t cg_tf32;               /* RBF only, 1: CG products in TF32 on tcgen05 (one term), each linear solve
+                                    iteratively refined against FP32 residuals to the same tolerance */
   int32_t verbose;               /* 1: one line per outer iteration on stderr */
 } kqr_options;
 
@@ -134,8 +136,10 @@ typedef struct kqr_options {
 typedef struct kqr_info {
   int32_t phase1_iters, phase2_iters, newton_steps, pcg_iters;
   int32_t matvecs_fp32, matvecs_high;  /* Gram products by arithmetic, each counted once per RHS */
+  int32_t matvecs_low;                 /* TF32 products (options.cg_tf32) */
   int32_t rank;                        /* preconditioner rank r */
   int32_t core_builds;                 /* Woodbury cores built (the rest of the systems reused one) */
+  int32_t cg_truncations;              /* CG runs stopped at a non-positive (rounding) curvature */
   double eta_p, eta_d, eta_c, eta_kkt, eta_gap, obj_p, obj_d;
   double sigma_final;
   double seconds;                      /* wall-clock of the solve */
@@ -155,7 +159,7 @@ void kqr_set_allocator(void* (*alloc)(size_t bytes, void* ctx), void (*free_fn)(
  * and y (host, n) to the device, prepares the tile layouts of X for the Gram
  * kernels, and builds the RPCholesky factor F (n x r) of K (Sec. 3), which
  * depends only on (X, kernel, gamma) and is reused by every later solve.
- * n >= 2, 1 <= p <= 128, gamma > 0, X and y finite.  opts may be NULL
+ * n >= 2, 1 <= p <= 64, gamma > 0, X and y finite.  opts may be NULL
  * (defaults).  On success *out owns all device memory of the problem. */
 kqr_status kqr_create(const double* X, const double* y, int64_t n, int64_t p, kqr_kernel kind,
                       double gamma, const kqr_options* opts, kqr_handle** out);
@@ -263,6 +267,53 @@ kqr_status kqr_refactor(kqr_handle* h, const double* pivot_uniforms);
  * Reading synchronises the handle's stream. */
 kqr_status kqr_profile(kqr_handle* h, int32_t enable);
 kqr_status kqr_profile_read(kqr_handle* h, int32_t kernel_id, int64_t* launches, double* total_ms);
+
+/* Held-out check loss of the last solve's fitted function and its gradient
+ * (an extension; the paper has no counterpart).  RBF kernel only.  X (host,
+ * n x p) must be the training inputs given to kqr_create; Xh (host, nh x p)
+ * and yh (host, nh) are held-out points.  With f(x) = beta + (1/lambda)
+ * sum_j alpha_j k(x_j, x) (Sec. 1), *loss = sum_h rho_tau(yh_h - f(xh_h)) and
+ * the derivatives of that loss with respect to log gamma, log lambda and the
+ * training inputs X (dX, host n x p row-major, nullable) are obtained by
+ * implicit differentiation through the KKT conditions of Sec. 4 at the
+ * solution, holding the elbow set {i : tau - 1 < alpha_i < tau} fixed (the
+ * loss is differentiable where no point enters or leaves it and no held-out
+ * residual is zero).  The Gram products are recomputed in tiles (FP32 for the
+ * adjoint terms, FP64-class for the held-out predictions); the adjoint solves
+ * use the problem's preconditioner, whose core this call replaces.  Allocates
+ * device memory; synchronises. */
+kqr_status kqr_heldout_grad(kqr_handle* h, const double* X, const double* Xh, const double* yh, int64_t nh,
+                            double* loss, double* d_loggamma, double* d_loglambda, double* dX);
+
+/* ---- batched multi-right-hand-side products ---------------------------------
+ * B independent RBF problems of different sizes (rows offsets[b] .. offsets[b+1]-1
+ * of X), each with its own gamma_b, and up to 64 right-hand sides per problem:
+ * U_b = K_b V_b with K_b[i][j] = exp(-gamma_b ||x_i - x_j||^2) (Sec. 1).  Fitting a
+ * grid of (tau, lambda) pairs on each data set needs products of the same K_b
+ * with one vector per pair (the ADMM and Newton systems of Sec. 3), so one
+ * pass over each Gram tile serves every pair.  Both contractions (X X^T and
+ * K V) run on the tensor cores in TF32 with FP32 accumulation: each entry
+ * of U carries a relative error of order 2^-10 of sum_j K_ij |V_jc|.
+ *
+ * Creates a handle for products only (the single-problem calls reject it;
+ * kqr_set_stream, kqr_profile(_read) with kernel id 0, kqr_launch_count,
+ * kqr_last_error and kqr_destroy apply).  X: host, offsets[B] x p row-major;
+ * offsets: host, B + 1 entries, offsets[0] = 0, strictly increasing;
+ * p in [1, 32]; gammas: host, B positive values.  The handle owns device
+ * copies; the caller keeps its arrays.  Synchronises. */
+kqr_status kqr_batch_create(const double* X, const int64_t* offsets, int64_t B, int64_t p, const double* gammas,
+                            kqr_handle** out);
+
+/* U = blockdiag(K_1 .. K_B) V for V (offsets[B] x m, row-major, rows ordered as
+ * X) with m in [1, 64]; U has the same layout.  Host pointers; allocates
+ * device staging buffers; synchronises; KQR_DEVICE_WAIT_TIMEOUT if the kernel
+ * gave up waiting on a copy. */
+kqr_status kqr_batch_kmatmul(kqr_handle* h, const double* V, double* U, int64_t m);
+
+/* As kqr_batch_kmatmul with device pointers, enqueued on the handle's stream;
+ * no allocation, no synchronisation.  Calls that overlap on the GPU share the
+ * handle's staging copy of V and race. */
+kqr_status kqr_batch_kmatmul_dev(kqr_handle* h, const double* V, double* U, int64_t m);
 
 /* Makes the handle enqueue its work on the given cudaStream_t (NULL: its own). */
 kqr_status kqr_set_stream(kqr_handle* h, void* stream);

@@ -477,3 +477,82 @@ def certified_gap(alpha, K, y, tau: float, lam: float, theta=None) -> dict:
     P = check_loss(r - beta, tau) + float(theta @ Kt) / (2.0 * lam)
     D = -float(a @ Ka) / (2.0 * lam) + float(y @ a)
     return dict(gap=(P - D) / (1.0 + abs(P) + abs(D)), P=P, D=D, beta=beta, alpha=a)
+
+
+# ---------------------------------------------------------------------------
+# Held-out check loss and its gradient by implicit differentiation (an
+# extension of the method: the paper has no counterpart; built on eq. (1.3),
+# the representer form of Sec. 1 and the Sec. 4 KKT conditions).
+#
+# With E = {i : tau - 1 < alpha_i < tau} (the elbow set) fixed, the KKT
+# conditions read F(alpha_E, beta; theta) = 0 with
+#   F_E = (K alpha)_E / lambda + beta - y_E,   F_last = 1^T alpha,
+# and alpha_i fixed at its bound off E.  The held-out loss is
+#   l = sum_h rho_tau(y_h - f(x_h)),  f(x) = beta + (1/lambda) sum_j alpha_j k(x_j, x).
+# With g_h = d rho_tau / d f (= -tau when y_h > f_h, 1 - tau when y_h < f_h),
+# a = [K_{E,h} g / lambda ; sum_h g_h] and J = [[K_EE / lambda, 1], [1^T, 0]],
+# solve J w = a; then for each parameter theta
+#   dl/dtheta = g^T (df_h/dtheta at fixed alpha, beta) - w^T (dF/dtheta at fixed alpha, beta).
+# ---------------------------------------------------------------------------
+def _sq_dists(X, Z):
+    diff = np.asarray(X, dtype=np.float64)[:, None, :] - np.asarray(Z, dtype=np.float64)[None, :, :]
+    return np.sum(diff * diff, axis=2)
+
+
+def heldout_loss(X, y, Xh, yh, gamma: float, tau: float, lam: float, tol: float = 1e-12,
+                 o: Options | None = None) -> dict:
+    """Solves the RBF problem on (X, y) and evaluates the held-out check loss
+    sum_h rho_tau(y_h - f(x_h)) of the representer-form predictor (Sec. 1)."""
+    K = gram(X, X, RBF, gamma)
+    res = solve_dense(K, y, tau, lam, tol, o)
+    f = predict(X, res["alpha"], res["beta"], Xh, RBF, gamma, lam)
+    return dict(loss=check_loss(np.asarray(yh) - f, tau), alpha=res["alpha"], beta=res["beta"], f=f, K=K, kkt=res["kkt"])
+
+
+def heldout_grad(X, y, Xh, yh, gamma: float, tau: float, lam: float, tol: float = 1e-12, edge: float = 1e-7) -> dict:
+    """Gradient of the held-out check loss with respect to log gamma, log
+    lambda and the training inputs X, by the implicit-function formula above,
+    with every partial derivative formed densely from its definition."""
+    X = np.asarray(X, dtype=np.float64)
+    Xh = np.asarray(Xh, dtype=np.float64)
+    yh = np.asarray(yh, dtype=np.float64)
+    n, p = X.shape
+    st = heldout_loss(X, y, Xh, yh, gamma, tau, lam, tol)
+    alpha, beta, f, K = st["alpha"], st["beta"], st["f"], st["K"]
+    Kh = gram(Xh, X, RBF, gamma)
+    D = _sq_dists(X, X)
+    Dh = _sq_dists(Xh, X)
+    r = yh - f
+    g = np.where(r > 0, -tau, 1.0 - tau)
+    E = np.flatnonzero((alpha > tau - 1.0 + edge) & (alpha < tau - edge))
+    m = E.size
+    J = np.zeros((m + 1, m + 1))
+    J[:m, :m] = K[np.ix_(E, E)] / lam
+    J[:m, m] = 1.0
+    J[m, :m] = 1.0
+    a = np.concatenate([Kh[:, E].T @ g / lam, [g.sum()]])
+    w = np.linalg.solve(J, a)
+    u = w[:m]
+
+    def total(dK, dKh, dlam_scale=None):
+        # explicit derivatives of f_h and F for a derivative dK of K (and dKh of Kh)
+        dfh = dKh @ alpha / lam
+        dFE = (dK @ alpha)[E] / lam
+        return float(g @ dfh - u @ dFE)
+
+    d_loglam = float(g @ (-(Kh @ alpha) / lam) - u @ (-(K @ alpha)[E] / lam))
+    d_loggam = total(-gamma * D * K, -gamma * Dh * Kh)
+    dX = np.zeros((n, p))
+    for k in range(n):
+        for c in range(p):
+            # d K_ij / d X_kc: row and column k of K, column k of Kh
+            dK = np.zeros((n, n))
+            col = -2.0 * gamma * (X[k, c] - X[:, c]) * K[k, :]
+            dK[k, :] = col
+            dK[:, k] = col
+            dK[k, k] = 0.0
+            dKh = np.zeros_like(Kh)
+            dKh[:, k] = -2.0 * gamma * (X[k, c] - Xh[:, c]) * Kh[:, k]
+            dX[k, c] = total(dK, dKh)
+    return dict(loss=st["loss"], d_loggamma=d_loggam, d_loglambda=d_loglam, dX=dX, elbow=E, g=g, w=w,
+                alpha=alpha, beta=beta)

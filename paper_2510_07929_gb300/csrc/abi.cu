@@ -154,11 +154,27 @@ bool make_tmap_rowmajor_sw128(CUtensorMap* tm, void* base, int64_t ldn, int Kp) 
          CUDA_SUCCESS;
 }
 
+// Tensor map over a 2-D FP32 array (inner extent, outer extent, row pitch in bytes) with
+// the 128-byte swizzle; box_inner x 4 must be 128 bytes.
+bool make_tmap_2d_f32_sw128(CUtensorMap* tm, void* base, int64_t inner, int64_t outer, int64_t row_bytes,
+                            int box_inner, int box_outer) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 static void free_all(Handle* h) {
   void* bufs[] = {h->xs32, h->nrm32, h->hq, h->hl, h->exp_table, h->xc64, h->y, h->F32, h->dres, h->core, h->tvec,
                   h->Linv, h->part, h->v32, h->vec_pool, h->scal, h->red_counter, h->red_part, h->err_flag,
                   h->st_alpha, h->st_v, h->st_z, h->sym_units, h->tc_hi, h->tc_lo};
   for (void* b : bufs) dev_free(h, b);
+  batch_free(h);
   if (h->scal_host) cudaFreeHost(h->scal_host);
   for (int k = 0; k < 2; ++k) {
     for (cudaEvent_t e : h->prof_ev[k]) cudaEventDestroy(e);
@@ -387,7 +403,13 @@ kqr_status kqr_set_stream(kqr_handle* kh, void* stream) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
   if (stream) {
+    // The caller keeps ownership of its stream; release ours.
+    if (h->own_stream && h->stream) {
+      cudaStreamSynchronize(h->stream);
+      cudaStreamDestroy(h->stream);
+    }
     h->stream = (cudaStream_t)stream;
+    h->own_stream = false;
   } else {
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return KQR_CUDA_ERROR;
@@ -403,6 +425,7 @@ kqr_status kqr_solve(kqr_handle* kh, double tau, double lambda, double tol, doub
                      kqr_info* info) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (!(tau > 0.0 && tau < 1.0)) return fail(h, KQR_INVALID_ARG, "tau must be in (0, 1)");
   if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(h, KQR_INVALID_ARG, "lambda must be positive");
   if (!(tol > 0.0)) return fail(h, KQR_INVALID_ARG, "tol must be positive");
@@ -423,6 +446,7 @@ kqr_status kqr_solve(kqr_handle* kh, double tau, double lambda, double tol, doub
 kqr_status kqr_get_state(kqr_handle* kh, double* v, double* z) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (!h->has_state) return fail(h, KQR_INVALID_ARG, "no solve has run on this handle");
   if (v && cudaMemcpy(v, h->st_v, sizeof(double) * h->n, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(h, KQR_CUDA_ERROR, "copy v");
@@ -434,6 +458,7 @@ kqr_status kqr_get_state(kqr_handle* kh, double* v, double* z) {
 kqr_status kqr_kmatvec_dev(kqr_handle* kh, const double* V, double* U, int64_t m, kqr_precision prec, void* stream) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (!V || !U) return fail(h, KQR_INVALID_ARG, "V and U must be non-null");
   if (m < 1 || m > kMaxRhs) return fail(h, KQR_INVALID_ARG, "m must be in [1, 8]");
   cudaStream_t st = pick_stream(h, stream);
@@ -451,6 +476,7 @@ kqr_status kqr_kmatvec_dev(kqr_handle* kh, const double* V, double* U, int64_t m
 kqr_status kqr_kmatvec(kqr_handle* kh, const double* V, double* U, int64_t m, kqr_precision prec) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (!V || !U) return fail(h, KQR_INVALID_ARG, "V and U must be non-null");
   if (m < 1 || m > kMaxRhs) return fail(h, KQR_INVALID_ARG, "m must be in [1, 8]");
   const size_t bytes = sizeof(double) * (size_t)h->n * m;
@@ -488,6 +514,7 @@ kqr_status kqr_box_grad_dev(kqr_handle* kh, const double* alpha, const double* z
                             double* Ldiag, double* grad_norm2, void* stream) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (!alpha || !z || !Kalpha) return fail(h, KQR_INVALID_ARG, "alpha, z and Kalpha must be non-null");
   if (!(sigma > 0) || !(lambda > 0) || !(tau > 0 && tau < 1)) return fail(h, KQR_INVALID_ARG, "bad sigma/lambda/tau");
   cudaStream_t st = pick_stream(h, stream);
@@ -507,6 +534,7 @@ kqr_status kqr_precond_apply_dev(kqr_handle* kh, const double* Ldiag, double gam
                                  void* stream) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (!Ldiag || !r || !out) return fail(h, KQR_INVALID_ARG, "null vector");
   if (!(gam > 0)) return fail(h, KQR_INVALID_ARG, "gam must be positive");
   cudaStream_t st = pick_stream(h, stream);
@@ -526,6 +554,7 @@ kqr_status kqr_pcg_dev(kqr_handle* kh, const double* Ldiag, double gam, const do
                        int32_t maxit, int32_t* iters, void* stream) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (!Ldiag || !b || !x) return fail(h, KQR_INVALID_ARG, "null vector");
   if (!(gam >= 0) || !(tol > 0) || maxit < 1) return fail(h, KQR_INVALID_ARG, "bad gam/tol/maxit");
   cudaStream_t st = pick_stream(h, stream);
@@ -548,6 +577,7 @@ kqr_status kqr_kkt(kqr_handle* kh, const double* alpha, const double* v, double 
                    double lambda, double* out7) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (!alpha || !v || !z || !out7) return fail(h, KQR_INVALID_ARG, "null pointer");
   const size_t bytes = sizeof(double) * h->n;
   double* buf = (double*)dev_alloc(h, bytes * 4);
@@ -569,8 +599,81 @@ kqr_status kqr_kkt(kqr_handle* kh, const double* alpha, const double* v, double 
 kqr_status kqr_refactor(kqr_handle* kh, const double* pivot_uniforms) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   h->has_state = false;
   return rpcholesky_setup(h, pivot_uniforms);
+}
+
+kqr_status kqr_batch_create(const double* X, const int64_t* offsets, int64_t B, int64_t p, const double* gammas,
+                            kqr_handle** out) {
+  if (!out) return KQR_INVALID_ARG;
+  *out = nullptr;
+  kqr_handle* kh = new (std::nothrow) kqr_handle();
+  if (!kh) return KQR_OOM;
+  *out = kh;
+  Handle* h = &kh->h;
+  h->alloc = g_alloc;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
+    return cuda_fail(h, e, "SM count");
+  if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(h, e, "stream");
+  h->own_stream = true;
+  h->err_flag = (int*)dev_alloc(h, 64);
+  if (!h->err_flag) return fail(h, KQR_OOM, "error flag");
+  if ((e = cudaMemsetAsync(h->err_flag, 0, 64, h->stream)) != cudaSuccess) return cuda_fail(h, e, "error flag");
+  kqr_status s = batch_create(h, X, offsets, B, p, gammas);
+  if (s != KQR_OK) return s;
+  h->n = offsets[B];
+  h->p = p;
+  h->kind = KQR_RBF;
+  return KQR_OK;
+}
+
+kqr_status kqr_batch_kmatmul_dev(kqr_handle* kh, const double* V, double* U, int64_t m) {
+  if (!kh) return KQR_INVALID_ARG;
+  Handle* h = &kh->h;
+  if (!h->batch) return fail(h, KQR_INVALID_ARG, "not a batch handle (kqr_batch_create)");
+  if (!V || !U) return fail(h, KQR_INVALID_ARG, "V and U must be non-null");
+  if (m < 1 || m > 64) return fail(h, KQR_INVALID_ARG, "m must be in [1, 64]");
+  cudaError_t e = batch_kmatmul(h, V, U, (int)m, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batched Gram product");
+  return KQR_OK;
+}
+
+kqr_status kqr_batch_kmatmul(kqr_handle* kh, const double* V, double* U, int64_t m) {
+  if (!kh) return KQR_INVALID_ARG;
+  Handle* h = &kh->h;
+  if (!h->batch) return fail(h, KQR_INVALID_ARG, "not a batch handle (kqr_batch_create)");
+  if (!V || !U) return fail(h, KQR_INVALID_ARG, "V and U must be non-null");
+  if (m < 1 || m > 64) return fail(h, KQR_INVALID_ARG, "m must be in [1, 64]");
+  const size_t bytes = sizeof(double) * (size_t)h->n * m;
+  double* dV = (double*)dev_alloc(h, bytes);
+  double* dU = (double*)dev_alloc(h, bytes);
+  kqr_status s = KQR_OK;
+  cudaError_t e = cudaSuccess;
+  if (!dV || !dU) {
+    s = fail(h, KQR_OOM, "batched product buffers");
+  } else {
+    e = cudaMemcpyAsync(dV, V, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+      s = kqr_batch_kmatmul_dev(kh, dV, dU, m);
+      if (s == KQR_OK) {
+        e = cudaMemcpyAsync(U, dU, bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      }
+    }
+    if (s == KQR_OK && e != cudaSuccess) s = cuda_fail(h, e, "batched product copies");
+  }
+  if (s == KQR_OK) {
+    int flag = 0;
+    if (cudaMemcpy(&flag, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && flag)
+      s = fail(h, KQR_DEVICE_WAIT_TIMEOUT, "the batched Gram kernel gave up waiting");
+  }
+  dev_free(h, dV);
+  dev_free(h, dU);
+  return s;
 }
 
 kqr_status kqr_profile(kqr_handle* kh, int32_t enable) {
@@ -601,6 +704,7 @@ kqr_status kqr_profile_read(kqr_handle* kh, int32_t kernel_id, int64_t* launches
 kqr_status kqr_get_factor(kqr_handle* kh, float* F, int64_t* pivots, int32_t* rank, int32_t* rank0) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (rank) *rank = h->r;
   if (rank0) *rank0 = h->r0;
   if (pivots)

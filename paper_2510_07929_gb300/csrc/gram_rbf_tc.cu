@@ -10,13 +10,17 @@
 // hi.hi + hi.lo + lo.hi (the lo.lo term is below FP32 rounding); one term
 // (hi.hi) gives the TF32 product.
 //
-// One CTA = 4 warps = 128 threads; thread t owns TMEM lane t = row t of the
-// tile, reads its 128 accumulators with tcgen05.ld and accumulates
-// exp2(...) v_j in registers, so rows need no cross-thread reduction.  Thread 0
-// issues the TMA copies and the MMAs.  Column tiles are split over
+// One CTA = 8 warps = 256 threads; thread t serves TMEM lane t mod 128 (row
+// t mod 128 of the tile) over column half t / 128, reads its 64 accumulators
+// with tcgen05.ld and accumulates exp2(...) v_j in registers (four independent
+// chains per right-hand side, so the FFMAs do not serialise); the two halves
+// of a row are added once at the end.  Thread 0 issues the TMA copies and the
+// MMAs.  Column tiles are split over
 // gridDim.y; per-split row sums are added in FP64 by a second kernel.
 // Every mbarrier wait is bounded; on a timeout the CTA records the error,
 // stops issuing work and frees its tensor memory.
+#include <vector>
+
 #include "kqr_internal.h"
 #include "ptx.cuh"
 
@@ -83,10 +87,11 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(const void* p) {
 constexpr uint32_t kAtomBytes = 128 * 128;   // 128 rows x 128 bytes (32 tf32 of K)
 
 template <int M, int NTERMS>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     gram_rbf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                        const float* __restrict__ nrm, const float* __restrict__ v32, float* __restrict__ part,
-                       int ksteps, int katoms, int ldn, int tiles_per_split, int col_tiles, int* __restrict__ err) {
+                       int ksteps, int katoms, int ldn, int tiles_per_split, int col_tiles, int fold_rows,
+                       int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~static_cast<uintptr_t>(1023));
@@ -97,11 +102,13 @@ __global__ void __launch_bounds__(128, 1)
   unsigned char* XJl[2] = {XIl + 2 * tb, XIl + 4 * tb};
   float* s_nrm = reinterpret_cast<float*>(XIl + 5 * tb);   // [2][128]
   float* s_v = s_nrm + 2 * 128;                             // [2][128 * M]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_v + 2 * 128 * M);  // 0: XI, 1-2: stages, 3-4: MMA buffers
+  float* s_red = s_v + 2 * 128 * M;                         // [128 * M] second-half row sums
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_red + 128 * M);  // 0: XI, 1-2: stages, 3-4: MMA buffers
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & 127, half = tid >> 7;
   const int row0 = blockIdx.x * 128;
   const int split = blockIdx.y;
   const int jt0 = split * tiles_per_split;
@@ -135,15 +142,21 @@ __global__ void __launch_bounds__(128, 1)
     if (nt > 0) load_tile(XJh[0], XJl[0], jt0 * 128, &bars[1]);
     if (nt > 1) load_tile(XJh[1], XJl[1], (jt0 + 1) * 128, &bars[2]);
   }
-  const float ni = nrm[row0 + tid];
-  float racc[M];
+  // K_ij = exp2(2 g_ij - n_j) exp2(-n_i): with fold_rows the row factor exp2(-n_i)
+  // multiplies the finished row sums instead of every entry (the host enables it
+  // only when max n_i is small enough that exp2(2 g - n_j) <= exp2(n_i) cannot overflow).
+  const float ni = nrm[row0 + row];
+  const float ni_in = fold_rows ? 0.f : ni;
+  float racc[M][4];
 #pragma unroll
-  for (int c = 0; c < M; ++c) racc[c] = 0.f;
+  for (int c = 0; c < M; ++c)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) racc[c][u] = 0.f;
   // kind::tf32, FP32 accumulate, A and B K-major, N = 128, M = 128
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
   for (int q = 0; q <= nt; ++q) {
-    if (q < nt) {
+    if (q < nt && tid < 128) {
       const int col = (jt0 + q) * 128 + tid;
       s_nrm[(q & 1) * 128 + tid] = __ldg(nrm + col);
 #pragma unroll
@@ -176,19 +189,25 @@ __global__ void __launch_bounds__(128, 1)
       const int b = pq & 1;
       if (mbar_wait_bounded(&bars[3 + b], (uint32_t)((pq >> 1) & 1), err)) {
         tc_fence_after();
-        const uint32_t tbase = tmem + (uint32_t)(b * 128) + ((uint32_t)(warp * 32) << 16);
-        const float* nj = s_nrm + b * 128;
-        const float* vj = s_v + b * 128 * M;
+        const uint32_t tbase = tmem + (uint32_t)(b * 128 + half * 64) + ((uint32_t)((warp & 3) * 32) << 16);
+        const float* nj = s_nrm + b * 128 + half * 64;
+        const float* vj = s_v + (b * 128 + half * 64) * M;
 #pragma unroll 1
-        for (int c4 = 0; c4 < 4; ++c4) {
+        for (int c4 = 0; c4 < 2; ++c4) {
           float g[32];
           tmem_ld32(tbase + (uint32_t)(c4 * 32), g);
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            const int col = c4 * 32 + jj;
-            const float e = ex2_approx(fmaf(2.f, g[jj], -(ni + nj[col])));
+          for (int j4 = 0; j4 < 8; ++j4) {
+            const float4 n4 = *reinterpret_cast<const float4*>(nj + c4 * 32 + j4 * 4);
+            const float nn[4] = {n4.x + ni_in, n4.y + ni_in, n4.z + ni_in, n4.w + ni_in};
 #pragma unroll
-            for (int c = 0; c < M; ++c) racc[c] = fmaf(e, vj[col * M + c], racc[c]);
+            for (int u = 0; u < 4; ++u) {
+              const int jj = j4 * 4 + u;
+              const int col = c4 * 32 + jj;
+              const float e = ex2_approx(fmaf(2.f, g[jj], -nn[u]));
+#pragma unroll
+              for (int c = 0; c < M; ++c) racc[c][u] = fmaf(e, vj[col * M + c], racc[c][u]);
+            }
           }
         }
       } else {
@@ -201,10 +220,20 @@ __global__ void __launch_bounds__(128, 1)
     // Stage (q + 1) & 1 held tile q - 1, whose MMAs completed above: refill it with tile q + 1.
     if (tid == 0 && q >= 1 && q + 1 < nt) load_tile(XJh[(q + 1) & 1], XJl[(q + 1) & 1], (jt0 + q + 1) * 128, &bars[1 + ((q + 1) & 1)]);
   }
+  float rs[M];
+  const float rowf = fold_rows ? ex2_approx(-ni) : 1.f;
 #pragma unroll
-  for (int c = 0; c < M; ++c) part[((size_t)split * ldn + row0 + tid) * M + c] = racc[c];
+  for (int c = 0; c < M; ++c) rs[c] = ((racc[c][0] + racc[c][1]) + (racc[c][2] + racc[c][3])) * rowf;
+  if (half == 1) {
+#pragma unroll
+    for (int c = 0; c < M; ++c) s_red[row * M + c] = rs[c];
+  }
   tc_fence_before();
   __syncthreads();
+  if (half == 0) {
+#pragma unroll
+    for (int c = 0; c < M; ++c) part[((size_t)split * ldn + row0 + row) * M + c] = rs[c] + s_red[row * M + c];
+  }
   if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
@@ -278,7 +307,7 @@ __global__ void tc_reduce_kernel(const float* __restrict__ part, int splits, int
 }
 
 static size_t tc_smem(int katoms, int M) {
-  return 1024 + (size_t)6 * katoms * kAtomBytes + (2 * 128 + 2 * 128 * (size_t)M) * sizeof(float) + 5 * 8 + 16;
+  return 1024 + (size_t)6 * katoms * kAtomBytes + (2 * 128 + 3 * 128 * (size_t)M) * sizeof(float) + 5 * 8 + 16;
 }
 
 bool make_tmap_rowmajor_sw128(CUtensorMap* tm, void* base, int64_t ldn, int Kp);
@@ -292,6 +321,16 @@ cudaError_t rbf_tc_prepare(Handle* h) {
   h->tc_lo = (float*)dev_alloc(h, bytes);
   if (!h->tc_hi || !h->tc_lo) return cudaErrorMemoryAllocation;
   h->tc_Kp = Kp;
+  // Fold the row factor exp2(-n_i) out of the entries when every n_i < 60:
+  // then exp2(2 g - n_j) <= exp2(n_i) < 2^60 stays finite in FP32.
+  {
+    std::vector<float> nrm((size_t)h->ldn);
+    cudaError_t e2 = cudaMemcpy(nrm.data(), h->nrm32, nrm.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e2 != cudaSuccess) return e2;
+    float mx = 0.f;
+    for (float v : nrm) mx = v > mx ? v : mx;
+    h->tc_fold_rows = mx < 60.f ? 1 : 0;
+  }
   tf32_split_kernel<<<grid_for(h->ldn * Kp), 256, 0, h->stream>>>(h->xs32, h->ldn, (int)h->p, Kp, h->tc_hi, h->tc_lo);
   h->launches++;
   cudaError_t e = cudaGetLastError();
@@ -311,8 +350,9 @@ static cudaError_t launch_tc(Handle* h, int splits, int tps, int ksteps, cudaStr
   if (e != cudaSuccess) return e;
   const int row_tiles = (int)(h->ldn / kTile);
   prof_mark(h, 0, true, st);
-  kern<<<dim3(row_tiles, splits), 128, smem, st>>>(h->tm_tc_hi, h->tm_tc_lo, h->nrm32, h->v32, h->part, ksteps,
-                                                   katoms, (int)h->ldn, tps, row_tiles, h->err_flag);
+  kern<<<dim3(row_tiles, splits), 256, smem, st>>>(h->tm_tc_hi, h->tm_tc_lo, h->nrm32, h->v32, h->part, ksteps,
+                                                   katoms, (int)h->ldn, tps, row_tiles, h->tc_fold_rows,
+                                                   h->err_flag);
   prof_mark(h, 0, false, st);
   h->launches++;
   return cudaGetLastError();

@@ -30,6 +30,7 @@ struct Allocator {
 };
 
 struct Handle;
+struct BatchData;
 
 // ---- device memory ---------------------------------------------------------
 void* dev_alloc(Handle* h, size_t bytes);
@@ -108,6 +109,7 @@ struct Handle {
   float* tc_hi = nullptr;
   float* tc_lo = nullptr;
   int tc_Kp = 0;
+  int tc_fold_rows = 0;   // apply exp2(-|xs_i|^2) to finished row sums (all norms < 60)
   CUtensorMap tm_tc_hi{}, tm_tc_lo{};
 
   // Symmetric Gram product: work-unit table (row tile, first and end column tile).
@@ -131,6 +133,7 @@ struct Handle {
   double* st_v = nullptr;
   double* st_z = nullptr;
   double st_beta = 0.0;
+  double st_tau = 0.0, st_lam = 0.0;   // (tau, lambda) of the last solve
   bool has_state = false;
 
   int64_t launches = 0;
@@ -140,6 +143,8 @@ struct Handle {
   std::vector<cudaEvent_t> prof_ev[2];
   size_t prof_used[2] = {0, 0};
   int num_sms = 0;
+  int64_t cg_truncations = 0;         // CG runs stopped at a non-positive curvature
+  BatchData* batch = nullptr;         // set for batched-product handles (batch.cu)
 };
 
 kqr_status fail(Handle* h, kqr_status s, const std::string& msg);
@@ -199,14 +204,20 @@ kqr_status rpcholesky_setup(Handle* h, const double* uniforms);
 // ---- solver (solver.cu) --------------------------------------------------------
 kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info);
 kqr_status pcg(Handle* h, const double* Ldiag, const double* Lpre, double gam, const double* b, double* x,
-               double* Kx, bool warm, double tol, int maxit, int* iters, cudaStream_t st);
+               double* Kx, bool warm, double tol, int maxit, int* iters, cudaStream_t st, bool lowprec = false);
+// PCG whose products use the one-term TF32 tensor-core RBF product, iteratively
+// refined against FP32 residuals until ||b - A x|| <= tol (FP32 operator);
+// Kx receives the FP32 K x.  Counts FP32 and TF32 products.
+kqr_status pcg_refined(Handle* h, const double* Ldiag, const double* Lpre, double gam, const double* b, double* x,
+                       double* Kx, bool warm, double tol, int maxit, int* iters, int* fp32_products,
+                       int* low_products, cudaStream_t st);
 kqr_status kkt(Handle* h, const double* alpha, const double* v, double beta, const double* z,
                const double* Kalpha, double tau, double lam, double* out7, cudaStream_t st);
 
 // Solver work vector slots in vec_pool.
 enum Vec {
   V_ALPHA = 0, V_V, V_Z, V_KALPHA, V_B, V_D, V_KD, V_R, V_ZZ, V_P, V_AP, V_KP, V_L, V_LPRE, V_GRAD,
-  V_S, V_TMP, V_TMP2, V_COUNT
+  V_S, V_TMP, V_TMP2, V_DX, V_RT, V_COUNT
 };
 inline double* vec(Handle* h, Vec v) { return h->vec_pool + (size_t)v * h->ldn; }
 
@@ -214,6 +225,30 @@ inline double* vec(Handle* h, Vec v) { return h->vec_pool + (size_t)v * h->ldn; 
 enum Scal { S_RED0 = 0, S_SUMP = 16, S_PAP = 17, S_A = 18, S_BETA = 19, S_RR = 20, S_RZ = 21, S_COUNT = 32 };
 
 // Launch configuration for element-wise kernels.
+// ---- batched multi-RHS products (batch.cu) ---------------------------------------
+struct BatchData {
+  int64_t B = 0, p = 0, R = 0;          // problems, features, padded rows (each problem to 128)
+  std::vector<int64_t> off, roff;       // row offsets: caller's (dense) and padded
+  int n_items = 0;
+  double entries = 0.0;                 // sum_b n_b^2
+  float* xt = nullptr;                  // [R][32] TF32 coordinates
+  float* nrm = nullptr;                 // [R] squared norms
+  float* vt = nullptr;                  // [64][R] TF32 right-hand sides
+  int* items = nullptr;                 // [n_items][4]
+  int* out0 = nullptr;                  // [n_items]
+  int64_t* d_off = nullptr;
+  int64_t* d_roff = nullptr;
+  CUtensorMap tm_xi, tm_xj, tm_v;
+};
+kqr_status batch_create(Handle* h, const double* X, const int64_t* offsets, int64_t B, int64_t p,
+                        const double* gammas);
+cudaError_t batch_kmatmul(Handle* h, const double* V, double* U, int m, cudaStream_t st);
+void batch_free(Handle* h);
+#define KQR_SINGLE(h)                                                                          \
+  do {                                                                                         \
+    if ((h)->batch) return fail((h), KQR_INVALID_ARG, "this call takes a single-problem handle"); \
+  } while (0)
+
 inline int grid_for(int64_t n, int threads = 256, int max_blocks = 1216) {
   int64_t b = (n + threads - 1) / threads;
   return (int)(b < 1 ? 1 : (b > max_blocks ? max_blocks : b));

@@ -43,6 +43,7 @@ extern "C" kqr_status kqr_kmatvec_fp32_noalloc_dev(kqr_handle* kh, const double*
                                                    void* stream) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
+  KQR_SINGLE(h);
   if (!V || !U) return fail(h, KQR_INVALID_ARG, "V and U must be non-null");
   if (m < 1 || m > kMaxRhs) return fail(h, KQR_INVALID_ARG, "m must be in [1, 8]");
   int dev = -1;

@@ -373,30 +373,54 @@ __global__ void chunk_sum_kernel(const double* __restrict__ d, int64_t n, int64_
   }
 }
 
-// Smallest s with cumsum(d)[s] > u * sum(d); writes s (or -1 if the sum is not positive).
-__global__ void pick_pivot_kernel(const double* __restrict__ d, int64_t n, int64_t chunk,
-                                  const double* __restrict__ csum, int nchunks, double u, long long* __restrict__ piv,
-                                  double* __restrict__ total_out) {
-  if (threadIdx.x != 0) return;
+// ---- fused RPCholesky steps ---------------------------------------------------------
+// One launch per pivot.  CTA b owns rows [b * kRpcChunk, (b + 1) * kRpcChunk); step t
+// forms column t of F for the pivot s = piv[t] chosen by the previous launch, updates the
+// residual diagonal and writes its chunk's sum of the new diagonal; the last CTA to finish
+// (a ticket counter, no waiting) draws the next pivot from the chunk sums.  state[0] is
+// the stop flag, state[1] the number of columns produced, state[2] the ticket counter.
+constexpr int kRpcChunk = 512;
+constexpr int kRpcThreads = 256;
+
+// Residual column entry g_i = k(x_i, x_s) - sum_{c<t} F[c][i] F[c][s]; every CTA calls it
+// for row s too, so the pivot's g_s is bit-identical to the one its own row computes.
+__device__ __forceinline__ double rpc_entry(const double* __restrict__ xc, int64_t ldn, int p, double gamma, int lap,
+                                            const double* __restrict__ F, int64_t n, int t, int64_t i,
+                                            const double* xs, const double* fs) {
+  double dist = 0.0;
+  for (int k = 0; k < p; ++k) {
+    const double v = xc[(size_t)k * ldn + i] - xs[k];
+    dist = lap ? dist + fabs(v) : fma(v, v, dist);
+  }
+  double acc = exp(-gamma * dist);
+  for (int c = 0; c < t; ++c) acc -= F[(size_t)c * n + i] * fs[c];
+  return acc;
+}
+
+// Pivot draw by the last CTA: the smallest s with running sum of d > u * sum(d), the
+// sums taken chunk by chunk in a fixed order.  Thread 0 only.
+__device__ void rpc_pick(const double* d, const double* csum, int64_t n, int nchunks, double u, long long* piv_out,
+                         int* state) {
   double total = 0.0;
-  for (int c = 0; c < nchunks; ++c) total += csum[c];
-  *total_out = total;
+  for (int c = 0; c < nchunks; ++c) total += __ldcg(csum + c);
   if (!(total > 0.0)) {
-    *piv = -1;
+    *piv_out = -1;
+    state[0] = 1;
     return;
   }
   const double target = u * total;
   double run = 0.0;
   int c = 0;
   for (; c < nchunks - 1; ++c) {
-    if (run + csum[c] > target) break;
-    run += csum[c];
+    const double cs = __ldcg(csum + c);
+    if (run + cs > target) break;
+    run += cs;
   }
-  int64_t s = (int64_t)c * chunk;
-  const int64_t end = min(n, s + chunk);
+  int64_t s = (int64_t)c * kRpcChunk;
+  const int64_t end = min(n, s + kRpcChunk);
   int64_t found = -1;
   for (; s < end; ++s) {
-    run += d[s];
+    run += __ldcg(d + s);
     if (run > target) {
       found = s;
       break;
@@ -404,40 +428,87 @@ __global__ void pick_pivot_kernel(const double* __restrict__ d, int64_t n, int64
   }
   if (found < 0) {  // rounding left the target past the last positive entry: take the last positive one
     for (int64_t q = n - 1; q >= 0; --q)
-      if (d[q] > 0.0) {
+      if (__ldcg(d + q) > 0.0) {
         found = q;
         break;
       }
   }
-  *piv = found;
+  *piv_out = found;
 }
 
-// g_i -= sum_{c<t} F[c][i] F[c][s]
-__global__ void rpc_residual_kernel(const double* __restrict__ F, int64_t n, int t, int64_t s,
-                                    double* __restrict__ g) {
-  extern __shared__ double fs[];
-  for (int c = threadIdx.x; c < t; c += blockDim.x) fs[c] = F[(size_t)c * n + s];
+__device__ __forceinline__ void rpc_chunk_sum_and_ticket(double local, double* csum, const double* d, int64_t n,
+                                                         int nchunks, const double* u, int t, int r0,
+                                                         long long* piv, int* state) {
+  __shared__ double ws[kRpcThreads / 32];
+  __shared__ int last;
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = local;
   __syncthreads();
-  GRID_LOOP(i, n) {
-    double acc = g[i];
-    for (int c = 0; c < t; ++c) acc -= F[(size_t)c * n + i] * fs[c];
-    g[i] = acc;
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kRpcThreads / 32; ++w) v += ws[w];
+    csum[blockIdx.x] = v;
+    __threadfence();
+    last = atomicAdd(state + 2, 1) == nchunks - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    state[2] = 0;
+    state[1] = t + 1;
+    if (t + 1 < r0) rpc_pick(d, csum, n, nchunks, u[t + 1], piv + t + 1, state);
   }
 }
 
-__global__ void rpc_column_kernel(const double* __restrict__ g, int64_t n, int64_t s, double* __restrict__ Fcol,
-                                  double* __restrict__ d, int* __restrict__ bad) {
-  const double gs = g[s];
-  if (!(gs > 0.0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *bad = 1;
+// d = diag(K) = 1 and the draw of the first pivot.
+__global__ void rpc_init_kernel(double* __restrict__ d, int64_t n, int nchunks, double* __restrict__ csum,
+                                const double* __restrict__ u, int r0, long long* __restrict__ piv,
+                                int* __restrict__ state) {
+  const int64_t i0 = (int64_t)blockIdx.x * kRpcChunk;
+  const int64_t i1 = min(n, i0 + kRpcChunk);
+  double local = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kRpcThreads) {
+    d[i] = 1.0;   // k(x, x) = 1 for the RBF and Laplacian kernels
+    local += 1.0;
+  }
+  rpc_chunk_sum_and_ticket(local, csum, d, n, nchunks, u, -1, r0, piv, state);
+}
+
+__global__ void __launch_bounds__(kRpcThreads) rpc_step_kernel(const double* __restrict__ xc, int64_t ldn, int p,
+                                                              double gamma, int lap, double* __restrict__ F,
+                                                              double* __restrict__ d, int64_t n, int t, int r0,
+                                                              int nchunks, double* __restrict__ csum,
+                                                              const double* __restrict__ u,
+                                                              long long* __restrict__ piv, int* __restrict__ state) {
+  if (*(volatile int*)state) return;   // an earlier step stopped the factorization
+  const long long s = piv[t];
+  extern __shared__ double sm[];
+  double* fs = sm;            // F[c][s], c < t
+  double* xs = sm + t;        // x_s
+  __shared__ double gs_sh;
+  for (int c = threadIdx.x; c < t; c += kRpcThreads) fs[c] = F[(size_t)c * n + s];
+  for (int k = threadIdx.x; k < p; k += kRpcThreads) xs[k] = xc[(size_t)k * ldn + s];
+  __syncthreads();
+  if (threadIdx.x == 0) gs_sh = rpc_entry(xc, ldn, p, gamma, lap, F, n, t, s, xs, fs);
+  __syncthreads();
+  const double gs = gs_sh;
+  if (!(gs > 0.0)) {     // the residual at the pivot vanished: stop with t columns
+    if (blockIdx.x == 0 && threadIdx.x == 0) state[0] = 1;
     return;
   }
   const double inv = 1.0 / sqrt(gs);
-  GRID_LOOP(i, n) {
-    const double f = g[i] * inv;
-    Fcol[i] = f;
-    d[i] = fmax(d[i] - f * f, 0.0);
+  const int64_t i0 = (int64_t)blockIdx.x * kRpcChunk;
+  const int64_t i1 = min(n, i0 + kRpcChunk);
+  double local = 0.0;
+  double* Ft = F + (size_t)t * n;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += kRpcThreads) {
+    const double f = rpc_entry(xc, ldn, p, gamma, lap, F, n, t, i, xs, fs) * inv;
+    Ft[i] = f;
+    const double di = fmax(d[i] - f * f, 0.0);
+    d[i] = di;
+    local += di;
   }
+  rpc_chunk_sum_and_ticket(local, csum, d, n, nchunks, u, t, r0, piv, state);
 }
 
 __global__ void to_float_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t cnt) {
@@ -530,14 +601,12 @@ kqr_status rpcholesky_setup(Handle* h, const double* uniforms) {
   const size_t fbytes = sizeof(double) * (size_t)r0 * n;
   double* F64 = (double*)dev_alloc(h, fbytes);
   double* d = (double*)dev_alloc(h, sizeof(double) * n);
-  double* g = (double*)dev_alloc(h, sizeof(double) * n);
   double* csum = (double*)dev_alloc(h, sizeof(double) * (kPivChunks + 8));
-  long long* piv_dev = (long long*)dev_alloc(h, sizeof(long long) * 2);
   int* bad = (int*)dev_alloc(h, sizeof(int) * 2);
   auto cleanup = [&]() {
-    dev_free(h, F64); dev_free(h, d); dev_free(h, g); dev_free(h, csum); dev_free(h, piv_dev); dev_free(h, bad);
+    dev_free(h, F64); dev_free(h, d); dev_free(h, csum); dev_free(h, bad);
   };
-  if (!F64 || !d || !g || !csum || !piv_dev || !bad) {
+  if (!F64 || !d || !csum || !bad) {
     cleanup();
     return fail(h, KQR_OOM, "RPCholesky workspace");
   }
@@ -556,43 +625,57 @@ kqr_status rpcholesky_setup(Handle* h, const double* uniforms) {
       u[t] = (double)(z >> 11) * (1.0 / 9007199254740992.0);
     }
   }
-  fill_L(h, d, 1.0, nullptr, n, st);   // diag(K) = 1
-  cudaMemsetAsync(bad, 0, sizeof(int) * 2, st);
   const int64_t chunk = (n + kPivChunks - 1) / kPivChunks;
   const int nchunks = (int)((n + chunk - 1) / chunk);
-  h->pivots.clear();
-  int t = 0;
-  double* total_dev = csum + kPivChunks;
-  for (; t < r0; ++t) {
-    chunk_sum_kernel<<<nchunks, 256, 0, st>>>(d, n, chunk, csum);
-    pick_pivot_kernel<<<1, 32, 0, st>>>(d, n, chunk, csum, nchunks, u[t], piv_dev, total_dev);
-    h->launches += 2;
-    long long s = -1;
-    if ((e = cudaMemcpyAsync(&s, piv_dev, sizeof(long long), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-      cleanup();
-      return cuda_fail(h, e, "pivot");
-    }
-    if (s < 0) break;
-    if ((e = gram_column(h, s, g, st)) != cudaSuccess) {
-      cleanup();
-      return cuda_fail(h, e, "K column");
-    }
-    if (t > 0) {
-      rpc_residual_kernel<<<grid_for(n), 256, sizeof(double) * t, st>>>(F64, n, t, s, g);
-      h->launches++;
-    }
-    rpc_column_kernel<<<grid_for(n), 256, 0, st>>>(g, n, s, F64 + (size_t)t * n, d, bad);
-    h->launches++;
-    int hbad = 0;
-    if ((e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-      cleanup();
-      return cuda_fail(h, e, "RPCholesky column");
-    }
-    if (hbad) break;
-    h->pivots.push_back(s);
+  const int rchunks = (int)((n + kRpcChunk - 1) / kRpcChunk);
+  double* u_dev = (double*)dev_alloc(h, sizeof(double) * (r0 + 1));
+  double* rsum = (double*)dev_alloc(h, sizeof(double) * (rchunks + 1));
+  long long* piv_all = (long long*)dev_alloc(h, sizeof(long long) * (r0 + 1));
+  int* state = (int*)dev_alloc(h, sizeof(int) * 4);
+  auto cleanup2 = [&]() { dev_free(h, u_dev); dev_free(h, rsum); dev_free(h, piv_all); dev_free(h, state); };
+  if (!u_dev || !rsum || !piv_all || !state) {
+    cleanup2();
+    cleanup();
+    return fail(h, KQR_OOM, "RPCholesky workspace");
   }
+  const size_t smem = sizeof(double) * ((size_t)r0 + h->p);
+  if (smem > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(rpc_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
+    cleanup2();
+    cleanup();
+    return cuda_fail(h, e, "RPCholesky shared memory (p too large)");
+  }
+  // All r0 steps are queued back to back; the device decides the pivots and when to stop.
+  if ((e = cudaMemcpyAsync(u_dev, u.data(), sizeof(double) * r0, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(state, 0, sizeof(int) * 4, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(piv_all, 0xff, sizeof(long long) * (r0 + 1), st)) != cudaSuccess) {
+    cleanup2();
+    cleanup();
+    return cuda_fail(h, e, "RPCholesky start");
+  }
+  rpc_init_kernel<<<rchunks, kRpcThreads, 0, st>>>(d, n, rchunks, rsum, u_dev, r0, piv_all, state);
+  h->launches++;
+  for (int t = 0; t < r0; ++t) {
+    rpc_step_kernel<<<rchunks, kRpcThreads, smem, st>>>(h->xc64, h->ldn, (int)h->p, h->gamma,
+                                                        h->kind == KQR_LAPLACIAN, F64, d, n, t, r0, rchunks, rsum,
+                                                        u_dev, piv_all, state);
+    h->launches++;
+  }
+  int hstate[4] = {0, 0, 0, 0};
+  std::vector<long long> hpiv(r0 + 1);
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaMemcpyAsync(hstate, state, sizeof(int) * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(hpiv.data(), piv_all, sizeof(long long) * (r0 + 1), cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+    cleanup2();
+    cleanup();
+    return cuda_fail(h, e, "RPCholesky steps");
+  }
+  cleanup2();
+  h->pivots.clear();
+  const int t = hstate[1];
+  for (int q = 0; q < t; ++q) h->pivots.push_back(hpiv[q]);
   const int rr0 = t;  // columns actually produced
   h->r0 = rr0;
   int r = rr0;

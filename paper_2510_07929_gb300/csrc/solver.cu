@@ -52,7 +52,7 @@ static kqr_status check_device_flag(Handle* h, cudaStream_t st) {
 }
 
 kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const double* b, double* x, double* Kx,
-               bool warm, double tol, int maxit, int* iters, cudaStream_t st) {
+               bool warm, double tol, int maxit, int* iters, cudaStream_t st, bool lowprec) {
   const int64_t n = h->n;
   double* r = vec(h, V_R);
   double* zz = vec(h, V_ZZ);
@@ -92,13 +92,27 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
     ep.pvec = p;
     ep.dot_out = h->scal + S_PAP;
     ep.raw_out = Kp;
-    CK(gram_f32(h, p, Ap, 1, &ep, st));
+    if (lowprec) CK(gram_rbf_tc(h, p, Ap, 1, false, &ep, st));
+    else CK(gram_f32(h, p, Ap, 1, &ep, st));
     CK(fetch(h, S_PAP, 1, st));
     const double pAp = h->scal_host[S_PAP];
-    if (!(pAp > 0.0) || !std::isfinite(pAp)) {
+    if (!std::isfinite(pAp)) {
       KS(check_device_flag(h, st));
       if (iters) *iters = it;
       return fail(h, KQR_BREAKDOWN, "CG: p^T A p = " + std::to_string(pAp));
+    }
+    if (!(pAp > 0.0)) {
+      // The operator is positive definite; a non-positive curvature is FP32 rounding in
+      // directions whose eigenvalues lie below the product's accuracy (a numerically
+      // low-rank K).  Truncate: keep x, or at the first step take the preconditioned
+      // residual itself (a Newton step with the preconditioner as the Hessian model).
+      if (it == 0) {
+        CK(put(h, S_A, 1.0, st));
+        CK(cg_update(h, x, Kx, r, p, Kp, Ap, h->scal + S_A, n, h->scal + S_RR, st));
+        ++it;
+      }
+      h->cg_truncations++;
+      break;
     }
     CK(put(h, S_A, rz / pAp, st));
     CK(cg_update(h, x, Kx, r, p, Kp, Ap, h->scal + S_A, n, h->scal + S_RR, st));
@@ -119,6 +133,62 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
   }
   if (iters) *iters = it;
   KS(check_device_flag(h, st));
+  return KQR_OK;
+}
+
+__global__ void residual_kernel(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ Ax,
+                                int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - Ax[i];
+}
+
+kqr_status pcg_refined(Handle* h, const double* L, const double* Lpre, double gam, const double* b, double* x,
+                       double* Kx, bool warm, double tol, int maxit, int* iters, int* fp32_products,
+                       int* low_products, cudaStream_t st) {
+  const int64_t n = h->n;
+  double* rt = vec(h, V_RT);
+  double* dx = vec(h, V_DX);
+  int total = 0, nf = 0, nl = 0;
+  if (!warm) {
+    CK(vec_fill(h, x, 0.0, n, st));
+    if (Kx) CK(vec_fill(h, Kx, 0.0, n, st));
+  }
+  const int max_rounds = 6;
+  for (int round = 0;; ++round) {
+    // FP32 residual of the current x (x = 0 needs no product).
+    if (round == 0 && !warm) {
+      CK(vec_copy(h, rt, b, n, st));
+    } else {
+      GramEpilogue ep;
+      ep.gam = gam;
+      ep.sum_p = h->scal + S_SUMP;
+      ep.L = L;
+      ep.pvec = x;
+      ep.raw_out = Kx;
+      CK(gram_f32(h, x, rt, 1, &ep, st));
+      ++nf;
+      residual_kernel<<<grid_for(n), 256, 0, st>>>(rt, b, rt, n);
+      h->launches++;
+      CK(cudaGetLastError());
+    }
+    RedArgs rn;
+    rn.a = rt;
+    CK(reduce(h, RED_NORM2, rn, n, h->scal + S_RR, st));
+    CK(fetch(h, S_RR, 1, st));
+    const double rr = std::sqrt(h->scal_host[S_RR]);
+    if (!std::isfinite(rr)) return fail(h, KQR_BREAKDOWN, "refined CG: non-finite residual");
+    if (rr <= tol || round == max_rounds) break;
+    // Correction from the TF32 operator: its ~1e-3 relative error limits one
+    // round to a ~1e-2 reduction, so do not ask for more.
+    int its = 0;
+    KS(pcg(h, L, Lpre, gam, rt, dx, nullptr, false, std::fmax(tol, 1e-2 * rr), maxit, &its, st, true));
+    total += its;
+    nl += its;
+    CK(axpy_vec(h, x, dx, 1.0, n, st));
+  }
+  if (iters) *iters = total;
+  if (fp32_products) *fp32_products += nf;
+  if (low_products) *low_products += nl;
   return KQR_OK;
 }
 
@@ -176,9 +246,11 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
   double* g = vec(h, V_GRAD);
   double* S = vec(h, V_S);
   const double* dres = (o.precond == KQR_PRECOND_NYSTROM_DIAG) ? h->dres : nullptr;
+  const bool mixed = o.cg_tf32 && h->kind == KQR_RBF;
   kqr_info inf{};
   inf.rank = h->r;
   const int64_t builds0 = h->core_builds;
+  const int64_t trunc0 = h->cg_truncations;
   double res[7] = {0, 0, 0, 0, 0, 0, 0};
   CK(vec_fill(h, alpha, 0.0, n, st));
   CK(vec_fill(h, v, 0.0, n, st));
@@ -209,9 +281,14 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
     // inexactness eps_k = admm_cg_rtol ||b_k|| / (k + 1)^1.5: summable while ||b_k|| stays bounded
     const double eps_k = o.admm_cg_rtol * std::sqrt(h->scal_host[S_RED0 + 15]) / std::pow(k + 1.0, 1.5);
     int its = 0;
-    KS(pcg(h, L, Lpre, lam * sigma, b, alpha, Ka, k > 0, eps_k, o.pcg_maxit, &its, st));
+    if (mixed) {
+      KS(pcg_refined(h, L, Lpre, lam * sigma, b, alpha, Ka, k > 0, eps_k, o.pcg_maxit, &its, &inf.matvecs_fp32,
+                     &inf.matvecs_low, st));
+    } else {
+      KS(pcg(h, L, Lpre, lam * sigma, b, alpha, Ka, k > 0, eps_k, o.pcg_maxit, &its, st));
+      inf.matvecs_fp32 += its;
+    }
     inf.pcg_iters += its;
-    inf.matvecs_fp32 += its;
     RedArgs rs;
     rs.a = alpha;
     CK(reduce(h, RED_SUM, rs, n, h->scal + S_RED0 + 11, st));
@@ -276,9 +353,14 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
         CK(scale_vec(h, b, g, -lam, n, st));
         const double ptol = lam * std::fmin(o.eta_bar, std::pow(ng, 1.0 + o.iota));
         int its = 0;
-        KS(pcg(h, L, Lpre, lam * sigma, b, d, Kd, false, ptol, o.pcg_maxit, &its, st));
+        if (mixed) {
+          KS(pcg_refined(h, L, Lpre, lam * sigma, b, d, Kd, false, ptol, o.pcg_maxit, &its, &inf.matvecs_fp32,
+                         &inf.matvecs_low, st));
+        } else {
+          KS(pcg(h, L, Lpre, lam * sigma, b, d, Kd, false, ptol, o.pcg_maxit, &its, st));
+          inf.matvecs_fp32 += its;
+        }
         inf.pcg_iters += its;
-        inf.matvecs_fp32 += its;
         // Armijo backtracking on phi_k(alpha + c d) - phi_k(alpha), term by term.
         CK(reduce_ls_pre(h, Ka, d, Kd, h->y, g, alpha, n, h->scal + S_RED0, st));
         CK(fetch(h, S_RED0, 6, st));
@@ -339,6 +421,8 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
   CK(vec_copy(h, h->st_z, z, n, st));
   CK(cudaStreamSynchronize(st));
   h->st_beta = beta;
+  h->st_tau = tau;
+  h->st_lam = lam;
   h->has_state = true;
   inf.eta_p = res[0];
   inf.eta_d = res[1];
@@ -349,6 +433,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
   inf.obj_d = res[6];
   inf.sigma_final = sigma;
   inf.core_builds = (int32_t)(h->core_builds - builds0);
+  inf.cg_truncations = (int32_t)(h->cg_truncations - trunc0);
   inf.seconds = now_s() - t_start;
   if (info) *info = inf;
   if (status != KQR_OK) return status;

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
         ("ssn_maxit", ctypes.c_int32), ("ls_maxit", ctypes.c_int32), ("pcg_maxit", ctypes.c_int32),
         ("core_reuse_rtol", ctypes.c_double),
         ("time_limit_s", ctypes.c_double), ("phase1_only", ctypes.c_int32),
-        ("symmetric_gram", ctypes.c_int32), ("rbf_tensor_cores", ctypes.c_int32), ("verbose", ctypes.c_int32),
+        ("symmetric_gram", ctypes.c_int32), ("rbf_tensor_cores", ctypes.c_int32), ("cg_tf32", ctypes.c_int32),
+        ("verbose", ctypes.c_int32),
     ]
 
 
@@ -47,7 +48,8 @@ class Info(ctypes.Structure):
     _fields_ = [
         ("phase1_iters", ctypes.c_int32), ("phase2_iters", ctypes.c_int32), ("newton_steps", ctypes.c_int32),
         ("pcg_iters", ctypes.c_int32), ("matvecs_fp32", ctypes.c_int32), ("matvecs_high", ctypes.c_int32),
-        ("rank", ctypes.c_int32), ("core_builds", ctypes.c_int32),
+        ("matvecs_low", ctypes.c_int32),
+        ("rank", ctypes.c_int32), ("core_builds", ctypes.c_int32), ("cg_truncations", ctypes.c_int32),
         ("eta_p", ctypes.c_double), ("eta_d", ctypes.c_double), ("eta_c", ctypes.c_double),
         ("eta_kkt", ctypes.c_double), ("eta_gap", ctypes.c_double), ("obj_p", ctypes.c_double),
         ("obj_d", ctypes.c_double), ("sigma_final", ctypes.c_double), ("seconds", ctypes.c_double),
@@ -79,6 +81,10 @@ SIGNATURES = {
     "kqr_get_factor": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "kqr_refactor": (ctypes.c_int, [_P, _DP]),
+    "kqr_heldout_grad": (ctypes.c_int, [_P, _DP, _DP, _DP, _I64, _DP, _DP, _DP, _DP]),
+    "kqr_batch_create": (ctypes.c_int, [_DP, ctypes.POINTER(_I64), _I64, _I64, _DP, ctypes.POINTER(_P)]),
+    "kqr_batch_kmatmul": (ctypes.c_int, [_P, _DP, _DP, _I64]),
+    "kqr_batch_kmatmul_dev": (ctypes.c_int, [_P, _P, _P, _I64]),
     "kqr_profile": (ctypes.c_int, [_P, _I32]),
     "kqr_profile_read": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I64), _DP]),
     "kqr_set_stream": (ctypes.c_int, [_P, _P]),
@@ -203,7 +209,7 @@ class Problem:
         beta = ctypes.c_double()
         kkt = ctypes.c_double()
         info = Info()
-        allow = (OK, NOT_CONVERGED) if allow_not_converged else (OK,)
+        allow = (OK, NOT_CONVERGED, TIMEOUT) if allow_not_converged else (OK,)
         st = self._check(self._lib.kqr_solve(self._h, tau, lam, tol, _dptr(alpha), ctypes.byref(beta),
                                              ctypes.byref(kkt), ctypes.byref(info)), allow)
         d = info.as_dict()
@@ -266,6 +272,18 @@ class Problem:
         F = F[:rank.value * self.n].reshape(rank.value, self.n).T
         return F, piv[:rank0.value], rank.value, rank0.value
 
+    def heldout_grad(self, Xh, yh, want_dX: bool = True):
+        """Held-out check loss of the last solve and its gradient with respect to
+        (log gamma, log lambda, X) (kqr_heldout_grad)."""
+        Xh = np.ascontiguousarray(Xh, dtype=np.float64)
+        yh = np.ascontiguousarray(yh, dtype=np.float64)
+        loss, dg, dl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        dX = np.empty_like(self.X) if want_dX else None
+        self._check(self._lib.kqr_heldout_grad(self._h, _dptr(self.X), _dptr(Xh), _dptr(yh), Xh.shape[0],
+                                               ctypes.byref(loss), ctypes.byref(dg), ctypes.byref(dl),
+                                               _dptr(dX) if want_dX else None))
+        return loss.value, dg.value, dl.value, dX
+
     def refactor(self, pivot_uniforms=None):
         u = None
         if pivot_uniforms is not None:
@@ -288,6 +306,77 @@ class Problem:
     @property
     def launches(self) -> int:
         return int(self._lib.kqr_launch_count(self._h))
+
+
+class Batch:
+    """B independent RBF problems (X_b n_b x p, gamma_b) for batched products
+    U_b = K_b V_b with up to 64 right-hand sides (kqr_batch_create)."""
+
+    def __init__(self, Xs, gammas):
+        self._lib = lib()
+        self.sizes = [int(x.shape[0]) for x in Xs]
+        self.p = int(Xs[0].shape[1])
+        self.X = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in Xs]))
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.gammas = np.ascontiguousarray(np.broadcast_to(np.asarray(gammas, dtype=np.float64), (len(Xs),)))
+        h = ctypes.c_void_p()
+        st = self._lib.kqr_batch_create(_dptr(self.X), self.offsets.ctypes.data_as(ctypes.POINTER(_I64)), len(Xs),
+                                        self.p, _dptr(self.gammas), ctypes.byref(h))
+        self._h = h
+        if st != OK:
+            msg = self._lib.kqr_last_error(h).decode() if h.value else ""
+            self.close()
+            raise KQRError(st, msg)
+        self.n = int(self.offsets[-1])
+
+    def _check(self, st: int):
+        if st != OK:
+            raise KQRError(st, self._lib.kqr_last_error(self._h).decode())
+
+    def kmatmul(self, V) -> np.ndarray:
+        """V: (sum n_b, m) host array, rows stacked like X; returns U of the same shape."""
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        V2 = V.reshape(self.n, -1)
+        U = np.empty_like(V2)
+        self._check(self._lib.kqr_batch_kmatmul(self._h, _dptr(V2), _dptr(U), V2.shape[1]))
+        return U.reshape(V.shape)
+
+    def kmatmul_dev(self, V, U):
+        m = 1 if V.dim() == 1 else V.shape[1]
+        self._check(self._lib.kqr_batch_kmatmul_dev(self._h, _tptr(V), _tptr(U), m))
+        return U
+
+    def set_stream(self, stream):
+        self._check(self._lib.kqr_set_stream(self._h, _stream_ptr(stream)))
+
+    def profile(self, enable: bool):
+        self._check(self._lib.kqr_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        cnt, ms = ctypes.c_int64(), ctypes.c_double()
+        self._check(self._lib.kqr_profile_read(self._h, 0, ctypes.byref(cnt), ctypes.byref(ms)))
+        return cnt.value, ms.value
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.kqr_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.kqr_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 _torch_alloc_refs = None
@@ -319,3 +408,30 @@ def use_torch_allocator():
 
 def use_cuda_allocator():
     lib().kqr_set_allocator(None, None, None)
+
+
+def heldout_check_loss(X, y, Xh, yh, log_gamma, log_lambda, tau: float, tol: float = 1e-8, **opts):
+    """Held-out check loss of the RBF kernel quantile regression fitted on
+    (X, y) at exp(log_gamma), exp(log_lambda), as a torch autograd function of
+    (X, log_gamma, log_lambda).  The forward pass is one kqr_solve and the
+    backward pass uses the gradients kqr_heldout_grad returns with the loss;
+    X, log_gamma and log_lambda are float64 CPU tensors (log_* 0-d)."""
+    import torch
+
+    class _HeldoutLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, Xt, lg, ll):
+            with Problem(Xt.detach().numpy(), y, "rbf", float(torch.exp(lg)), **opts) as prob:
+                prob.solve(tau, float(torch.exp(ll)), tol)
+                loss, dg, dl, dX = prob.heldout_grad(Xh, yh, want_dX=Xt.requires_grad)
+            ctx.save_for_backward(torch.from_numpy(dX) if dX is not None else torch.zeros(0, dtype=torch.float64),
+                                  torch.tensor(dg, dtype=torch.float64), torch.tensor(dl, dtype=torch.float64))
+            ctx.want_dX = dX is not None
+            return torch.tensor(loss, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, go):
+            dX, dg, dl = ctx.saved_tensors
+            return (go * dX if ctx.want_dX else None), go * dg, go * dl
+
+    return _HeldoutLoss.apply(X, log_gamma, log_lambda)

@@ -1,0 +1,101 @@
+"""Held-out loss gradients on the GPU (kqr_heldout_grad) against the oracle's
+dense implicit-differentiation formula, and against central finite
+differences of GPU solves at a size the dense formula cannot reach."""
+import numpy as np
+import pytest
+
+from oracle import kqr_oracle as O
+from paper_2510_07929_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K_():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07929_gb300 import build
+
+    build.build()
+    from paper_2510_07929_gb300 import kqr
+
+    return kqr
+
+
+def _split(n, nh, p, seed, tau, lam):
+    tr = W.rbf_small(n=n, p=p, seed=seed, tau=tau, lam=lam)
+    ho = W.rbf_small(n=nh, p=p, seed=seed + 1000, tau=tau, lam=lam)
+    return tr, ho.X, ho.y
+
+
+@pytest.mark.parametrize("n,nh,p,tau,lam,gamma,tc", [(300, 200, 4, 0.5, 1e-2, 0.5, 1),
+                                                     (257, 131, 3, 0.3, 5e-2, 1.0, 0),
+                                                     (390, 170, 6, 0.7, 2e-2, 0.25, 1)])
+def test_heldout_grad_matches_oracle(K_, n, nh, p, tau, lam, gamma, tc):
+    tr, Xh, yh = _split(n, nh, p, 3, tau, lam)
+    ref = O.heldout_grad(tr.X, tr.y, Xh, yh, gamma, tau, lam)
+    with K_.Problem(tr.X, tr.y, "rbf", gamma, rbf_tensor_cores=tc) as prob:
+        prob.solve(tau, lam, 1e-10)
+        loss, dg, dl, dX = prob.heldout_grad(Xh, yh)
+    scale = 1.0 + abs(ref["loss"])
+    assert abs(loss - ref["loss"]) <= 1e-7 * scale, (loss, ref["loss"])
+    # FP32 Gram products in the adjoint terms: relative 1e-4 of the gradient's scale
+    assert abs(dl - ref["d_loglambda"]) <= 1e-4 * scale, (dl, ref["d_loglambda"])
+    assert abs(dg - ref["d_loggamma"]) <= 1e-4 * scale, (dg, ref["d_loggamma"])
+    err = np.abs(dX - ref["dX"]).max()
+    assert err <= 1e-4 * (1.0 + np.abs(ref["dX"]).max()), err
+
+
+def test_heldout_grad_finite_differences(K_):
+    """n = 3000 training and 1000 held-out points: log-lambda and log-gamma
+    derivatives against central differences of GPU solves (the loss is piecewise
+    smooth; the step is small enough that no point changes side)."""
+    tau, lam = 0.5, 1e-2
+    tr, Xh, yh = _split(3000, 1000, 8, 11, tau, lam)
+    gamma = tr.gamma
+
+    def loss_at(gm, lm):
+        with K_.Problem(tr.X, tr.y, "rbf", gm) as prob:
+            prob.solve(tau, lm, 1e-10)
+            return prob.heldout_grad(Xh, yh, want_dX=False)
+
+    loss, dg, dl, _ = loss_at(gamma, lam)
+    h = 1e-4
+    fd_l = (loss_at(gamma, lam * np.exp(h))[0] - loss_at(gamma, lam * np.exp(-h))[0]) / (2 * h)
+    fd_g = (loss_at(gamma * np.exp(h), lam)[0] - loss_at(gamma * np.exp(-h), lam)[0]) / (2 * h)
+    scale = 1.0 + abs(loss)
+    assert abs(fd_l - dl) <= 2e-4 * scale, (fd_l, dl)
+    assert abs(fd_g - dg) <= 2e-4 * scale, (fd_g, dg)
+
+
+def test_heldout_grad_rejects_bad_calls(K_):
+    tr, Xh, yh = _split(200, 50, 3, 5, 0.5, 1e-2)
+    with K_.Problem(tr.X, tr.y, "rbf", 0.5) as prob:
+        with pytest.raises(K_.KQRError):
+            prob.heldout_grad(Xh, yh)          # no solve yet
+    lap = W.lap_large(n=300, p=4)
+    with K_.Problem(lap.X, lap.y, "laplacian", lap.gamma) as prob:
+        prob.solve(lap.tau, 1e-2, 1e-6)
+        with pytest.raises(K_.KQRError):
+            prob.heldout_grad(lap.X[:20], lap.y[:20])
+
+
+def test_autograd_wrapper_matches_entry_point(K_):
+    import torch
+
+    tau, lam, gamma = 0.5, 2e-2, 0.4
+    tr, Xh, yh = _split(400, 150, 5, 21, tau, lam)
+    with K_.Problem(tr.X, tr.y, "rbf", gamma) as prob:
+        prob.solve(tau, lam, 1e-9)
+        loss, dg, dl, dX = prob.heldout_grad(Xh, yh)
+    Xt = torch.tensor(tr.X, requires_grad=True)
+    lg = torch.tensor(np.log(gamma), dtype=torch.float64, requires_grad=True)
+    ll = torch.tensor(np.log(lam), dtype=torch.float64, requires_grad=True)
+    out = K_.heldout_check_loss(Xt, tr.y, Xh, yh, lg, ll, tau, tol=1e-9)
+    (2.0 * out).backward()
+    assert float(out) == pytest.approx(loss, rel=1e-9)
+    assert float(lg.grad) == pytest.approx(2 * dg, rel=1e-3, abs=1e-6)
+    assert float(ll.grad) == pytest.approx(2 * dl, rel=1e-3, abs=1e-6)
+    assert np.abs(Xt.grad.numpy() - 2 * dX).max() <= 1e-3 * (1 + np.abs(dX).max())

@@ -67,6 +67,16 @@ def test_solve_matches_oracle(K_, name, n, tau):
     check_against_oracle(wl, alpha, beta, v, z, kkt)
 
 
+@pytest.mark.parametrize("name,n", [("rbf_small", 2000), ("rbf_mid", 2500)])
+def test_mixed_precision_solve_matches_oracle(K_, name, n):
+    """CG products in TF32 on the tensor cores, each solve refined against FP32
+    residuals: the same parity contract as the FP32 solver."""
+    wl = W.GENERATORS[name](n=n)
+    alpha, beta, v, z, kkt, info = gpu_solve(K_, wl, tol=1e-7, cg_tf32=1)
+    assert info["matvecs_low"] > 0
+    check_against_oracle(wl, alpha, beta, v, z, kkt)
+
+
 @pytest.mark.parametrize("precond", [1, 2])
 def test_paper_preconditioner_and_plain_cg_converge(K_, precond):
     wl = W.rbf_small(n=900, seed=5)
