@@ -30,6 +30,9 @@ METRIC = "KQR solve sec to KKT≤1e-6 at n=200k; fused K·V TFLOP/s and % of roo
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) per launch of gram_f32_sym_kernel on the n = 200000, p = 50
+# Laplacian workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
+SYM_LAPLACIAN_TRAFFIC = {(200000, 50): 42469632 + 8192}
 # Gram products (FP32 + FP64-class) of one solve of the default workload with
 # the library's default constants; the reference arm, which cannot run the
 # solver, scales the oracle's per-product time by it.
@@ -296,8 +299,9 @@ def run_ours(args):
             flops_per_entry = 2 * p + 5
         peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # Top/s, FP32 pipe lane-ops
         achieved = entries * ops_per_entry / avg_s / 1e12
+        traffic = SYM_LAPLACIAN_TRAFFIC.get((n, p)) if wl.kind == "laplacian" else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "gram_f32_sym_kernel (FP32 Gram tiles, symmetric)",
+                    "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": "gram_f32_sym_kernel (FP32 Gram tiles, symmetric)",
                     "launches": n32, "avg_ms": ms32 / n32, "entries_per_launch": entries,
                     "kv_tflops_effective": float(n) * n * flops_per_entry / avg_s / 1e12,
                     "peak_basis": "152 SM x 128 FP32 lanes x 2070 MHz (derived, not measured)"}
@@ -472,9 +476,9 @@ def run_path(args):
 
 def run_grad(args):
     """Held-out loss gradient on the n = 20000 (+ 5000 held-out) p = 16 RBF
-    workload (gamma = 1/16, lambda = 1e-2, tau = 0.5): seconds of the forward
-    solve and of kqr_heldout_grad, with a central-difference check of the
-    log-lambda and log-gamma derivatives from four more solves."""
+    workload (x ~ U[0,1]^16, gamma = 0.25, lambda = 0.1, tau = 0.5): seconds of
+    the forward solve and of kqr_heldout_grad, with a central-difference check
+    of the log-lambda and log-gamma derivatives from four more solves."""
     import torch
 
     from paper_2510_07929_gb300 import build, workloads as W
@@ -484,10 +488,10 @@ def run_grad(args):
 
     n = args.n or 20000
     nh = max(1, n // 4)
-    tau, lam, tol = 0.5, 1e-2, 1e-8
+    tau, lam, tol = 0.5, 0.1, 1e-8
     tr = W.rbf_small(n=n, p=16, seed=0, tau=tau, lam=lam)
     ho = W.rbf_small(n=nh, p=16, seed=1000, tau=tau, lam=lam)
-    gamma = 1.0 / 16
+    gamma = 0.25
 
     def fwd(gm, lm, grad=True):
         with kqr.Problem(tr.X, tr.y, "rbf", gm) as prob:
@@ -504,7 +508,7 @@ def run_grad(args):
     h = 1e-4
     fl = [fwd(gamma, lam * np.exp(s * h), False)[0][0] for s in (1, -1)]
     fg = [fwd(gamma * np.exp(s * h), lam, False)[0][0] for s in (1, -1)]
-    out = {"mode": "grad", "workload": f"rbf n={n} + {nh} held-out, p=16, gamma=1/16, lambda={lam:g}, tau={tau:g}",
+    out = {"mode": "grad", "workload": f"rbf n={n} + {nh} held-out, p=16, gamma={gamma:g}, lambda={lam:g}, tau={tau:g}",
            "solve_s": t_solve, "grad_s": t_grad, "kkt": kkt, "loss": loss, "d_loglambda": dl, "d_loggamma": dg,
            "dX_max_abs": float(np.abs(dX).max()),
            "fd_d_loglambda": (fl[0] - fl[1]) / (2 * h), "fd_d_loggamma": (fg[0] - fg[1]) / (2 * h),

@@ -509,7 +509,8 @@ def heldout_loss(X, y, Xh, yh, gamma: float, tau: float, lam: float, tol: float 
     return dict(loss=check_loss(np.asarray(yh) - f, tau), alpha=res["alpha"], beta=res["beta"], f=f, K=K, kkt=res["kkt"])
 
 
-def heldout_grad(X, y, Xh, yh, gamma: float, tau: float, lam: float, tol: float = 1e-12, edge: float = 1e-7) -> dict:
+def heldout_grad(X, y, Xh, yh, gamma: float, tau: float, lam: float, tol: float = 1e-12, edge: float = 1e-7,
+                 want_dX: bool = True) -> dict:
     """Gradient of the held-out check loss with respect to log gamma, log
     lambda and the training inputs X, by the implicit-function formula above,
     with every partial derivative formed densely from its definition."""
@@ -542,8 +543,8 @@ def heldout_grad(X, y, Xh, yh, gamma: float, tau: float, lam: float, tol: float 
 
     d_loglam = float(g @ (-(Kh @ alpha) / lam) - u @ (-(K @ alpha)[E] / lam))
     d_loggam = total(-gamma * D * K, -gamma * Dh * Kh)
-    dX = np.zeros((n, p))
-    for k in range(n):
+    dX = np.zeros((n, p)) if want_dX else None
+    for k in range(n if want_dX else 0):
         for c in range(p):
             # d K_ij / d X_kc: row and column k of K, column k of Kh
             dK = np.zeros((n, n))

@@ -83,7 +83,7 @@ __global__ void colstats_kernel(const double* __restrict__ X, int64_t n, int p, 
 // Feature-major layouts of the centred data (padding rows i >= n are zero):
 //   xc64 = x - mean; xs32 = float(scale * xc64); Laplacian fixed point hq, hl of scale * xc64.
 __global__ void layout_kernel(const double* __restrict__ X, const double* __restrict__ stats, int64_t n, int64_t ldn,
-                              int p, double scale, int lap, int G, double* __restrict__ xc64, float* __restrict__ xs32,
+                              int p, double scale, int fixed, int G, double* __restrict__ xc64, float* __restrict__ xs32,
                               int32_t* __restrict__ hq, float* __restrict__ hl) {
   const double twoG = ldexp(1.0, G), twomG = ldexp(1.0, -G);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ldn * p; e += (int64_t)gridDim.x * blockDim.x) {
@@ -93,7 +93,7 @@ __global__ void layout_kernel(const double* __restrict__ X, const double* __rest
     xc64[e] = x;
     const double xs = scale * x;
     xs32[e] = (float)xs;
-    if (lap) {
+    if (fixed) {
       const double H = rint(xs * twoG);
       hq[e] = (int32_t)H;
       hl[e] = (float)(xs - H * twomG);
@@ -219,7 +219,10 @@ static kqr_status create(Handle* h, const double* X, const double* y, int64_t n,
   h->nrm32 = (float*)dev_alloc(h, ldn * 4);
   h->xc64 = (double*)dev_alloc(h, fe * 8);
   h->y = (double*)dev_alloc(h, ldn * 8);
-  if (kind == KQR_LAPLACIAN) {
+  // Fixed-point layout for the FP64-class products: every Laplacian problem, and RBF
+  // problems with p <= kRbfEmuMaxP (the emulated RBF product's shared-memory limit).
+  const bool fixed_point = kind == KQR_LAPLACIAN || p <= kRbfEmuMaxP;
+  if (fixed_point) {
     h->hq = (int32_t*)dev_alloc(h, fe * 4);
     h->hl = (float*)dev_alloc(h, fe * 4);
     h->exp_table = (float2*)dev_alloc(h, sizeof(float2) << kExpTableBits);
@@ -234,7 +237,7 @@ static kqr_status create(Handle* h, const double* X, const double* y, int64_t n,
   h->st_z = (double*)dev_alloc(h, ldn * 8);
   double* Xd = (double*)dev_alloc(h, (size_t)n * p * 8);
   double* stats = (double*)dev_alloc(h, (size_t)p * 3 * 8);
-  if (!h->xs32 || !h->nrm32 || !h->xc64 || !h->y || (kind == KQR_LAPLACIAN && (!h->hq || !h->hl || !h->exp_table)) ||
+  if (!h->xs32 || !h->nrm32 || !h->xc64 || !h->y || (fixed_point && (!h->hq || !h->hl || !h->exp_table)) ||
       !h->vec_pool || !h->scal || !h->red_counter || !h->red_part || !h->err_flag || !h->st_alpha || !h->st_v ||
       !h->st_z || !Xd || !stats) {
     dev_free(h, Xd);
@@ -267,16 +270,24 @@ static kqr_status create(Handle* h, const double* X, const double* y, int64_t n,
   const double g2 = gamma / std::log(2.0);
   const double scale = kind == KQR_LAPLACIAN ? g2 : std::sqrt(g2);
   int G = 0;
-  if (kind == KQR_LAPLACIAN) {
+  if (fixed_point) {
     double R = 0.0;
     for (int64_t k = 0; k < p; ++k) R = std::fmax(R, (hs[3 * k + 2] - hs[3 * k + 1]) * scale);
-    // sum_k |hq_ik - hq_jk| <= p R 2^G must stay below 2^30 (int32 with a spare bit)
-    G = R > 0 ? (int)std::floor(std::log2(((double)(1 << 30) - 1.0) / ((double)p * R))) : 33;
-    if (G > 33) G = 33;
-    if (G < kExpTableBits + 1) {
+    if (kind == KQR_LAPLACIAN) {
+      // sum_k |hq_ik - hq_jk| <= p R 2^G must stay below 2^30 (int32 with a spare bit)
+      G = R > 0 ? (int)std::floor(std::log2(((double)(1 << 30) - 1.0) / ((double)p * R))) : 33;
+      if (G > 33) G = 33;
+    } else {
+      // sum_k (hq_ik - hq_jk)^2 <= p (R 2^G)^2 must stay below 2^62 (int64 with a spare bit);
+      // G <= 28 keeps the sub-table remainder (< 2^(2G - 10)) within two 23-bit floats
+      G = R > 0 ? (int)std::floor(std::log2(2147483000.0 / (R * std::sqrt((double)p)))) : 28;
+      if (G > 28) G = 28;
+    }
+    const int Gmin = kind == KQR_LAPLACIAN ? kExpTableBits + 1 : 17;
+    if (G < Gmin) {
       dev_free(h, Xd);
       dev_free(h, stats);
-      return fail(h, KQR_INVALID_ARG, "gamma * data range too large for the high-precision Laplacian layout");
+      return fail(h, KQR_INVALID_ARG, "gamma * data range too large for the high-precision fixed-point layout");
     }
     h->grid_G = G;
     std::vector<float2> tab(1 << kExpTableBits);
@@ -287,7 +298,7 @@ static kqr_status create(Handle* h, const double* X, const double* y, int64_t n,
     }
     cudaMemcpyAsync(h->exp_table, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
   }
-  layout_kernel<<<grid_for(ldn * p), 256, 0, st>>>(Xd, stats, n, ldn, (int)p, scale, kind == KQR_LAPLACIAN, G, h->xc64,
+  layout_kernel<<<grid_for(ldn * p), 256, 0, st>>>(Xd, stats, n, ldn, (int)p, scale, fixed_point ? 1 : 0, G, h->xc64,
                                                     h->xs32, h->hq, h->hl);
   norms_kernel<<<grid_for(ldn), 256, 0, st>>>(h->xs32, ldn, (int)p, h->nrm32);
   h->launches += 2;
@@ -297,7 +308,7 @@ static kqr_status create(Handle* h, const double* X, const double* y, int64_t n,
   if (e != cudaSuccess) return cuda_fail(h, e, "layout");
   if (!make_tmap(&h->tm_xs32, h->xs32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ldn, p))
     return fail(h, KQR_CUDA_ERROR, "cuTensorMapEncodeTiled failed for the FP32 layout");
-  if (kind == KQR_LAPLACIAN) {
+  if (fixed_point) {
     if (!make_tmap(&h->tm_hq, h->hq, CU_TENSOR_MAP_DATA_TYPE_INT32, ldn, p) ||
         !make_tmap(&h->tm_hl, h->hl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ldn, p))
       return fail(h, KQR_CUDA_ERROR, "cuTensorMapEncodeTiled failed for the fixed-point layout");

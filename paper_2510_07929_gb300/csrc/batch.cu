@@ -14,12 +14,13 @@
 // positive semidefinite), P rounded to TF32 (nearest) and V rounded to TF32.
 //
 // Work item = (problem, 128-row tile); its 64-column steps stream X_J and V_J
-// through a 4-stage TMA ring.  Items are sorted by length and dealt round-robin
-// to one persistent CTA per SM.  Warp roles (192 threads): warp 0 issues TMA
-// copies, warp 1 owns tensor memory and issues the MMAs, warps 2-5 are the
-// epilogue (thread = TMEM lane = row).  Tensor memory: two S buffers and two U
-// accumulators (64 columns each), so the exp of step q overlaps the MMAs of
-// steps q - 1 and q + 1 and the read-out of item i overlaps item i + 1.
+// through TMA rings of 4 and 5 stages.  Items are sorted by length and dealt
+// round-robin to one persistent CTA per SM.  Warp roles (320 threads): warp 0
+// issues TMA copies, warp 1 owns tensor memory and issues the MMAs, warps 2-9
+// are the epilogue (thread = TMEM lane = row; two warps per lane group split the
+// 64 columns).  Tensor memory: four S buffers and two U accumulators (64 columns
+// each); the first MMAs run two steps ahead of the second ones, so the epilogue
+// finds its next S tile computed, and the read-out of item i overlaps item i + 1.
 // Every wait is bounded; a timeout sets the error flag and an abort flag that
 // ends every role's loop, after which the CTA drains its copies and MMAs and
 // frees its tensor memory.
@@ -37,7 +38,12 @@ namespace {
 constexpr int kBM = 128;      // rows per work item (TMEM lanes)
 constexpr int kBN = 64;       // Gram columns per step = K of the second MMA
 constexpr int kBR = 64;       // right-hand sides = N of the second MMA
-constexpr int kStages = 4;
+constexpr int kXStages = 4;                 // X_J ring (released after the first MMA)
+constexpr int kVStages = 5;                 // V_J ring (released after the second MMA)
+constexpr int kSBufs = 4;                   // S tiles in tensor memory
+constexpr int kLookahead = 2;               // first MMAs issued ahead of the second ones
+constexpr int kEpiWarps = 8;                // two per SM sub-partition, 32 columns each
+constexpr int kBatchThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kXIBytes = kBM * 128;    // 128 rows x 128 B (32 TF32 features, zero padded)
 constexpr uint32_t kXJBytes = kBN * 128;    // 64 rows x 128 B
 constexpr uint32_t kVAtom = kBR * 128;      // 64 right-hand sides x 32 columns
@@ -46,11 +52,12 @@ constexpr uint32_t kPAtom = kBM * 128;      // 128 rows x 32 columns
 constexpr uint32_t kPBytes = 2 * kPAtom;
 constexpr uint32_t kOffXI = 0;
 constexpr uint32_t kOffXJ = kOffXI + 2 * kXIBytes;
-constexpr uint32_t kOffV = kOffXJ + kStages * kXJBytes;
-constexpr uint32_t kOffP = kOffV + kStages * kVBytes;
+constexpr uint32_t kOffV = kOffXJ + kXStages * kXJBytes;
+constexpr uint32_t kOffP = kOffV + kVStages * kVBytes;
 constexpr uint32_t kOffBar = kOffP + 2 * kPBytes;
-constexpr int kNumBars = 2 + 2 + kStages + kStages + 2 + 2 + 2 + 2 + 2 + 2 + 1;
+constexpr int kNumBars = 2 + 2 + 2 * kXStages + 2 * kVStages + 2 * kSBufs + 2 + 2 + 2 + 2 + 1;
 constexpr size_t kBatchSmem = 1024 + kOffBar + kNumBars * 8 + 16;
+constexpr uint32_t kUCol = 64 * kSBufs;     // first TMEM column of the U accumulators
 
 __device__ __forceinline__ void tmem_alloc_b(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
@@ -142,7 +149,7 @@ struct MmaStep {
 
 // items[i] = {row0 (padded row of the tile), col0 (padded first row of its problem),
 //             nt (64-column steps), nvalid (rows < n_b in the tile)}; out0[i] = output row of row0.
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kBatchThreads, 1)
     batch_kv_kernel(const __grid_constant__ CUtensorMap tm_xi, const __grid_constant__ CUtensorMap tm_xj,
                     const __grid_constant__ CUtensorMap tm_v, const float* __restrict__ nrm,
                     const int4* __restrict__ items, const int* __restrict__ out0, int n_items, int ksteps,
@@ -154,11 +161,13 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + kOffBar);
   uint64_t* xi_full = bars;
   uint64_t* xi_empty = bars + 2;
-  uint64_t* ld_full = bars + 4;
-  uint64_t* ld_empty = ld_full + kStages;
-  uint64_t* s_full = ld_empty + kStages;
-  uint64_t* s_empty = s_full + 2;
-  uint64_t* p_full = s_empty + 2;
+  uint64_t* xl_full = bars + 4;
+  uint64_t* xl_empty = xl_full + kXStages;
+  uint64_t* vl_full = xl_empty + kXStages;
+  uint64_t* vl_empty = vl_full + kVStages;
+  uint64_t* s_full = vl_empty + kVStages;
+  uint64_t* s_empty = s_full + kSBufs;
+  uint64_t* p_full = s_empty + kSBufs;
   uint64_t* p_empty = p_full + 2;
   uint64_t* u_full = p_empty + 2;
   uint64_t* u_empty = u_full + 2;
@@ -168,23 +177,29 @@ __global__ void __launch_bounds__(192, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 1) {
-    tmem_alloc_b(tmem_slot, 256);
+    tmem_alloc_b(tmem_slot, 512);
     tmem_relinquish_b();
   }
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&xi_full[i], 1);
       mbar_init(&xi_empty[i], 1);
-      mbar_init(&s_full[i], 1);
-      mbar_init(&s_empty[i], 4);
-      mbar_init(&p_full[i], 4);
+      mbar_init(&p_full[i], kEpiWarps);
       mbar_init(&p_empty[i], 1);
       mbar_init(&u_full[i], 1);
-      mbar_init(&u_empty[i], 4);
+      mbar_init(&u_empty[i], kEpiWarps);
     }
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&ld_full[s], 1);
-      mbar_init(&ld_empty[s], 1);
+    for (int i = 0; i < kSBufs; ++i) {
+      mbar_init(&s_full[i], 1);
+      mbar_init(&s_empty[i], kEpiWarps);
+    }
+    for (int i = 0; i < kXStages; ++i) {
+      mbar_init(&xl_full[i], 1);
+      mbar_init(&xl_empty[i], 1);
+    }
+    for (int i = 0; i < kVStages; ++i) {
+      mbar_init(&vl_full[i], 1);
+      mbar_init(&vl_empty[i], 1);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -201,46 +216,52 @@ __global__ void __launch_bounds__(192, 1)
     // ---- TMA producer ----
     if (lane == 0) {
       int q = 0, seq = 0;
-      for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++seq) {
+      bool ok = true;
+      for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
         const int4 I = items[it];
         const int xb = seq & 1;
         if (!bwait(&xi_empty[xb], ((seq >> 1) & 1) ^ 1, abort_flag, err)) break;
         mbar_arrive_expect_tx(&xi_full[xb], kXIBytes);
         tma_load_2d(base + kOffXI + xb * kXIBytes, &tm_xi, 0, I.x, &xi_full[xb]);
-        bool ok = true;
-        for (int j = 0; j < I.z; ++j, ++q) {
-          const int s = q % kStages;
-          if (!bwait(&ld_empty[s], ((q / kStages) & 1) ^ 1, abort_flag, err)) {
+        ++seq;
+        for (int j = 0; j < I.z; ++j) {
+          const int xs = q % kXStages, vs = q % kVStages;
+          const int c0 = I.y + j * kBN;
+          if (!bwait(&xl_empty[xs], ((q / kXStages) & 1) ^ 1, abort_flag, err)) {
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&ld_full[s], kXJBytes + kVBytes);
-          const int c0 = I.y + j * kBN;
-          tma_load_2d(base + kOffXJ + s * kXJBytes, &tm_xj, 0, c0, &ld_full[s]);
-          tma_load_2d(base + kOffV + s * kVBytes, &tm_v, c0, 0, &ld_full[s]);
-          tma_load_2d(base + kOffV + s * kVBytes + kVAtom, &tm_v, c0 + 32, 0, &ld_full[s]);
-        }
-        if (!ok) {
-          ++seq;
-          break;
+          mbar_arrive_expect_tx(&xl_full[xs], kXJBytes);
+          tma_load_2d(base + kOffXJ + xs * kXJBytes, &tm_xj, 0, c0, &xl_full[xs]);
+          if (!bwait(&vl_empty[vs], ((q / kVStages) & 1) ^ 1, abort_flag, err)) {
+            ok = false;
+            ++q;                         // the X_J copy of this step is in flight
+            break;
+          }
+          mbar_arrive_expect_tx(&vl_full[vs], kVBytes);
+          tma_load_2d(base + kOffV + vs * kVBytes, &tm_v, c0, 0, &vl_full[vs]);
+          tma_load_2d(base + kOffV + vs * kVBytes + kVAtom, &tm_v, c0 + 32, 0, &vl_full[vs]);
+          ++q;
         }
       }
       // Drain: every copy this thread issued has landed before the CTA exits.
       for (int k = (seq > 2 ? seq - 2 : 0); k < seq; ++k) dwait(&xi_full[k & 1], (k >> 1) & 1);
-      for (int k = (q > kStages ? q - kStages : 0); k < q; ++k) dwait(&ld_full[k % kStages], (k / kStages) & 1);
+      for (int k = (q > kXStages ? q - kXStages : 0); k < q; ++k) dwait(&xl_full[k % kXStages], (k / kXStages) & 1);
+      for (int k = (q > kVStages ? q - kVStages : 0); k < q; ++k) dwait(&vl_full[k % kVStages], (k / kVStages) & 1);
     }
   } else if (warp == 1) {
-    // ---- MMA issuer ----
+    // ---- MMA issuer: first MMAs run kLookahead steps ahead of the second ones ----
     if (lane == 0) {
-      int q = 0, seq = 0;
-      MmaStep prev = {-1, 0, 0, 0, 0};
+      int q = 0, q2 = 0, seq = 0;
+      MmaStep rec[kSBufs];
       bool ok = true;
       auto second = [&](const MmaStep& ps, int qq) -> bool {
         const int pb = qq & 1;
         if (!bwait(&p_full[pb], (qq >> 1) & 1, abort_flag, err)) return false;
+        if (!bwait(&vl_full[ps.stage], (qq / kVStages) & 1, abort_flag, err)) return false;
         if (ps.first && !bwait(&u_empty[ps.ub], ((ps.item_seq >> 1) & 1) ^ 1, abort_flag, err)) return false;
         fence_after();
-        const uint32_t d = tmem + 128u + (uint32_t)(ps.ub * 64);
+        const uint32_t d = tmem + kUCol + (uint32_t)(ps.ub * 64);
         const uint32_t pa = sbase + kOffP + pb * kPBytes;
         const uint32_t va = sbase + kOffV + ps.stage * kVBytes;
 #pragma unroll
@@ -250,45 +271,53 @@ __global__ void __launch_bounds__(192, 1)
                    (ps.first && k == 0) ? 0u : 1u);
         }
         mma_commit(&p_empty[pb]);
-        mma_commit(&ld_empty[ps.stage]);
+        mma_commit(&vl_empty[ps.stage]);
         if (ps.last) mma_commit(&u_full[ps.ub]);
         return true;
       };
       for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++seq) {
         const int4 I = items[it];
         const int xb = seq & 1;
-        if (!bwait(&xi_full[xb], (seq >> 1) & 1, abort_flag, err)) break;
+        if (!bwait(&xi_full[xb], (seq >> 1) & 1, abort_flag, err)) {
+          ok = false;
+          break;
+        }
         const uint32_t xa = sbase + kOffXI + xb * kXIBytes;
-        for (int j = 0; j < I.z; ++j, ++q) {
-          const int s = q % kStages;
-          const int sb = q & 1;
-          if (!bwait(&ld_full[s], (q / kStages) & 1, abort_flag, err) ||
-              !bwait(&s_empty[sb], ((q >> 1) & 1) ^ 1, abort_flag, err)) {
+        for (int j = 0; j < I.z; ++j) {
+          const int xs = q % kXStages, sb = q % kSBufs;
+          if (!bwait(&xl_full[xs], (q / kXStages) & 1, abort_flag, err) ||
+              !bwait(&s_empty[sb], ((q / kSBufs) & 1) ^ 1, abort_flag, err)) {
             ok = false;
             break;
           }
           fence_after();
-          const uint32_t ja = sbase + kOffXJ + s * kXJBytes;
+          const uint32_t ja = sbase + kOffXJ + xs * kXJBytes;
           const uint32_t d = tmem + (uint32_t)(sb * 64);
           for (int k = 0; k < ksteps; ++k)
             mma_tf32(d, desc_sw128(xa + (uint32_t)k * 32u), desc_sw128(ja + (uint32_t)k * 32u), idesc, k > 0 ? 1u : 0u);
           mma_commit(&s_full[sb]);
+          mma_commit(&xl_empty[xs]);
           if (j == I.z - 1) mma_commit(&xi_empty[xb]);
-          if (prev.stage >= 0 && !second(prev, q - 1)) {
-            ok = false;
-            break;
+          rec[sb] = {q % kVStages, seq & 1, seq, j == 0 ? 1 : 0, j == I.z - 1 ? 1 : 0};
+          ++q;
+          while (ok && q2 < q - kLookahead) {
+            if (!second(rec[q2 % kSBufs], q2)) ok = false;
+            ++q2;
           }
-          prev = {s, seq & 1, seq, j == 0 ? 1 : 0, j == I.z - 1 ? 1 : 0};
         }
       }
-      if (ok && prev.stage >= 0) second(prev, q - 1);
+      while (ok && q2 < q) {
+        if (!second(rec[q2 % kSBufs], q2)) ok = false;
+        ++q2;
+      }
       // Drain: all MMAs issued by this thread have completed.
       mma_commit(drain);
       dwait(drain, 0);
     }
   } else {
-    // ---- epilogue: thread = TMEM lane = row of the item ----
-    const int lg = warp & 3;
+    // ---- epilogue: thread = TMEM lane = row of the item; warp half ch owns columns [32 ch, 32 ch + 32) ----
+    const int lg = warp & 3;                  // TMEM lane group this warp may access
+    const int ch = (warp - 2) >> 2;           // column half
     const int r = lg * 32 + lane;
     const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
     int q = 0, seq = 0;
@@ -297,22 +326,21 @@ __global__ void __launch_bounds__(192, 1)
       const int4 I = items[it];
       const float ni = __ldg(nrm + I.x + r);
       for (int j = 0; j < I.z; ++j, ++q) {
-        const int sb = q & 1;
-        if (!bwait(&s_full[sb], (q >> 1) & 1, abort_flag, err)) {
+        const int sb = q % kSBufs;
+        if (!bwait(&s_full[sb], (q / kSBufs) & 1, abort_flag, err)) {
           ok = false;
           break;
         }
         fence_after();
-        float g[64];
-        tmem_load32(tmem + (uint32_t)(sb * 64) + lane_off, g);
-        tmem_load32(tmem + (uint32_t)(sb * 64 + 32) + lane_off, g + 32);
+        float g[32];
+        tmem_load32(tmem + (uint32_t)(sb * 64 + ch * 32) + lane_off, g);
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive_1(&s_empty[sb]);
-        const float4* nj4 = reinterpret_cast<const float4*>(nrm + I.y + j * kBN);
-        uint32_t e[64];
+        const float4* nj4 = reinterpret_cast<const float4*>(nrm + I.y + j * kBN + ch * 32);
+        uint32_t e[32];
 #pragma unroll
-        for (int c4 = 0; c4 < 16; ++c4) {
+        for (int c4 = 0; c4 < 8; ++c4) {
           const float4 nn = __ldg(nj4 + c4);
           e[4 * c4 + 0] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 0], -(ni + nn.x))));
           e[4 * c4 + 1] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 1], -(ni + nn.y))));
@@ -324,13 +352,12 @@ __global__ void __launch_bounds__(192, 1)
           ok = false;
           break;
         }
-        unsigned char* prow = base + kOffP + pb * kPBytes + r * 128;
+        // columns [32 ch, 32 ch + 32) are swizzle atom ch of the P tile
+        unsigned char* prow = base + kOffP + pb * kPBytes + ch * kPAtom + r * 128;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int atom = c >> 3, chunk = (c & 7) ^ (r & 7);
-          *reinterpret_cast<uint4*>(prow + atom * kPAtom + chunk * 16) =
+        for (int c = 0; c < 8; ++c)
+          *reinterpret_cast<uint4*>(prow + ((c ^ (r & 7)) * 16)) =
               make_uint4(e[4 * c], e[4 * c + 1], e[4 * c + 2], e[4 * c + 3]);
-        }
         fence_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive_1(&p_full[pb]);
@@ -339,24 +366,24 @@ __global__ void __launch_bounds__(192, 1)
       const int ub = seq & 1;
       if (!bwait(&u_full[ub], (seq >> 1) & 1, abort_flag, err)) break;
       fence_after();
-      float u[64];
-      tmem_load32(tmem + 128u + (uint32_t)(ub * 64) + lane_off, u);
-      tmem_load32(tmem + 128u + (uint32_t)(ub * 64 + 32) + lane_off, u + 32);
+      float u[32];
+      tmem_load32(tmem + kUCol + (uint32_t)(ub * 64 + ch * 32) + lane_off, u);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_1(&u_empty[ub]);
       if (r < I.w) {
-        double* o = out + (size_t)(out0[it] + r) * m;
+        double* o = out + (size_t)(out0[it] + r) * m + ch * 32;
+        const int mc = m - ch * 32;
 #pragma unroll
-        for (int c = 0; c < 64; ++c)
-          if (c < m) o[c] = (double)u[c];
+        for (int c = 0; c < 32; ++c)
+          if (c < mc) o[c] = (double)u[c];
       }
     }
   }
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 1) tmem_dealloc_b(tmem, 256);
+  if (warp == 1) tmem_dealloc_b(tmem, 512);
 }
 
 // Row-major padded TF32 coordinates xt[R][32] and squared norms of the rounded rows.
@@ -539,7 +566,7 @@ cudaError_t batch_kmatmul(Handle* h, const double* V, double* U, int m, cudaStre
   const int grid = std::min(h->num_sms, bd->n_items);
   const int ksteps = (int)((bd->p + 7) / 8);
   prof_mark(h, 0, true, st);
-  batch_kv_kernel<<<grid, 192, kBatchSmem, st>>>(bd->tm_xi, bd->tm_xj, bd->tm_v, bd->nrm,
+  batch_kv_kernel<<<grid, kBatchThreads, kBatchSmem, st>>>(bd->tm_xi, bd->tm_xj, bd->tm_v, bd->nrm,
                                                  reinterpret_cast<const int4*>(bd->items), bd->out0, bd->n_items,
                                                  ksteps, U, m, h->err_flag);
   prof_mark(h, 0, false, st);

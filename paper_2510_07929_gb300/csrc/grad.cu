@@ -29,9 +29,12 @@ namespace kqr {
 #define GRID_LOOP(i, n) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// Block sum of v added atomically to *out.  The leading barrier keeps a second call in the
+// same kernel from overwriting ws while thread 0 still reads the first call's values.
 __device__ __forceinline__ void block_add(double v, double* out) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __shared__ double ws[32];
+  __syncthreads();
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -15,7 +15,8 @@
 //   table of 2^(-k/1024), r < 2^-10 handled by a degree-4 Taylor polynomial
 //   whose two leading terms are kept in double-float (Tang's table method).
 //   Row sums of K_ij v_j are double-float (TwoSum accumulation), then FP64.
-// RBF: plain FP64 entries and sums (used at the sizes where that is cheap).
+// RBF: the same fixed-point scheme on squared differences (p <= kRbfEmuMaxP), else
+// plain FP64 entries and sums.
 #include <cmath>
 
 #include "kqr_internal.h"
@@ -205,6 +206,217 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid < kTile) part[(size_t)split * ldn + row0 + tid] = red[tid] + red[kTile + tid];
 }
 
+// RBF, FP64-class on the FP32/INT32 pipes (p <= kRbfEmuMaxP):
+//   xs = sqrt(gamma log2 e)(x - mean) = hq 2^-G + hl as for the Laplacian, with G
+//   chosen so that sum_k (hq_ik - hq_jk)^2 < 2^62.  With dH = hq_ik - hq_jk (exact
+//   int), dl = hl_ik - hl_jk and dx = xs32_ik - xs32_jk (the FP32 coordinates),
+//   (dH 2^-G + dl)^2 = dH^2 2^-2G + (2 (dH 2^-G + dl) - dl) dl, so
+//   D_ij = sum_k (xs_ik - xs_jk)^2 = Q 2^-2G + W,  Q = sum dH^2 (exact int64),
+//   W = sum (2 dx - dl) dl (FP32; replacing dH 2^-G + dl by dx costs
+//   2 |dx| 2^-24 |dl| <= 2^-(G+22) |dx| per feature, far below D's FP64-class error).
+//   K_ij = 2^-D by the same table method as the Laplacian, the sub-table part
+//   r = (Q mod 2^(2G-10)) 2^-2G + W carried in double-float.
+// Thread tile 8 rows x 4 columns (the int64 sums need the registers); a 128-column
+// TMA tile is processed as two 64-column halves.
+__global__ void __launch_bounds__(kThreads, 1)
+    gram_rbf_emu_kernel(const __grid_constant__ CUtensorMap tm_h, const __grid_constant__ CUtensorMap tm_l,
+                        const __grid_constant__ CUtensorMap tm_x, const float2* __restrict__ vhl,
+                        const float2* __restrict__ table, double* __restrict__ part, int p, int ldn, int G,
+                        int tiles_per_split, int col_tiles, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int tile_elems = p * kTile;
+  int32_t* HI = reinterpret_cast<int32_t*>(smem_raw);
+  float* LI = reinterpret_cast<float*>(HI + tile_elems);
+  float* XI = LI + tile_elems;
+  int32_t* HJ[2];
+  float* LJ[2];
+  float* XJ[2];
+  HJ[0] = reinterpret_cast<int32_t*>(XI + tile_elems);
+  LJ[0] = reinterpret_cast<float*>(HJ[0] + tile_elems);
+  XJ[0] = LJ[0] + tile_elems;
+  HJ[1] = reinterpret_cast<int32_t*>(XJ[0] + tile_elems);
+  LJ[1] = reinterpret_cast<float*>(HJ[1] + tile_elems);
+  XJ[1] = LJ[1] + tile_elems;
+  float2* tab = reinterpret_cast<float2*>(XJ[1] + tile_elems);
+  double* red = reinterpret_cast<double*>(tab + (1 << kTB));  // 2 x 128 doubles
+  uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * kTile);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ty = (warp >> 1) * 4 + (lane >> 3);
+  const int tx = (warp & 1) * 8 + (lane & 7);
+  const int row0 = blockIdx.x * kTile;
+  const int split = blockIdx.y;
+  const int jt0 = split * tiles_per_split;
+  const int jt1 = min(col_tiles, jt0 + tiles_per_split);
+  const uint32_t bytes = (uint32_t)tile_elems * 4u;
+
+  for (int i = tid; i < (1 << kTB); i += kThreads) tab[i] = table[i];
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bars[0], 3 * bytes);
+    tma_load_2d(HI, &tm_h, row0, 0, &bars[0]);
+    tma_load_2d(LI, &tm_l, row0, 0, &bars[0]);
+    tma_load_2d(XI, &tm_x, row0, 0, &bars[0]);
+    if (jt0 < jt1) {
+      mbar_arrive_expect_tx(&bars[1], 3 * bytes);
+      tma_load_2d(HJ[0], &tm_h, jt0 * kTile, 0, &bars[1]);
+      tma_load_2d(LJ[0], &tm_l, jt0 * kTile, 0, &bars[1]);
+      tma_load_2d(XJ[0], &tm_x, jt0 * kTile, 0, &bars[1]);
+    }
+  }
+  float s_hi[8], s_lo[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) s_hi[a] = s_lo[a] = 0.f;
+  const int sh = 2 * G - kTB;                                   // bits below the table index
+  const long long mask_r = (1LL << sh) - 1;
+  const int mask_f = (1 << kTB) - 1;
+  const float scaleA = __int_as_float((127 + 23 - 2 * G) << 23);  // 2^(23 - 2G)
+  const float scaleB = __int_as_float((127 - 2 * G) << 23);       // 2^-2G
+
+  if (!mbar_wait_bounded(&bars[0], 0, err)) return;
+
+  for (int t = jt0; t < jt1; ++t) {
+    const int q = t - jt0;
+    const int s = q & 1;
+    if (tid == 0 && t + 1 < jt1) {
+      const int ns = (q + 1) & 1;
+      mbar_arrive_expect_tx(&bars[1 + ns], 3 * bytes);
+      tma_load_2d(HJ[ns], &tm_h, (t + 1) * kTile, 0, &bars[1 + ns]);
+      tma_load_2d(LJ[ns], &tm_l, (t + 1) * kTile, 0, &bars[1 + ns]);
+      tma_load_2d(XJ[ns], &tm_x, (t + 1) * kTile, 0, &bars[1 + ns]);
+    }
+    if (!mbar_wait_bounded(&bars[1 + s], (uint32_t)((q >> 1) & 1), err)) return;
+    const int32_t* HJs = HJ[s];
+    const float* LJs = LJ[s];
+    const float* XJs = XJ[s];
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      const int cj = half * 64 + tx * 4;             // column within the tile
+      const int col0 = t * kTile + cj;
+      float vh[4], vl[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float2 w = __ldg(vhl + col0 + b);
+        vh[b] = w.x;
+        vl[b] = w.y;
+      }
+      long long Q[8][4];
+      float W[8][4];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          Q[a][b] = 0;
+          W[a][b] = 0.f;
+        }
+      for (int k = 0; k < p; ++k) {
+        const int4 h0 = *reinterpret_cast<const int4*>(HI + k * kTile + ty * 8);
+        const int4 h1 = *reinterpret_cast<const int4*>(HI + k * kTile + ty * 8 + 4);
+        const float4 l0 = *reinterpret_cast<const float4*>(LI + k * kTile + ty * 8);
+        const float4 l1 = *reinterpret_cast<const float4*>(LI + k * kTile + ty * 8 + 4);
+        const float4 x0 = *reinterpret_cast<const float4*>(XI + k * kTile + ty * 8);
+        const float4 x1 = *reinterpret_cast<const float4*>(XI + k * kTile + ty * 8 + 4);
+        const int4 g0 = *reinterpret_cast<const int4*>(HJs + k * kTile + cj);
+        const float4 m0 = *reinterpret_cast<const float4*>(LJs + k * kTile + cj);
+        const float4 y0 = *reinterpret_cast<const float4*>(XJs + k * kTile + cj);
+        const int ha[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+        const float la[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+        const float xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        const int hb[4] = {g0.x, g0.y, g0.z, g0.w};
+        const float lb[4] = {m0.x, m0.y, m0.z, m0.w};
+        const float xb[4] = {y0.x, y0.y, y0.z, y0.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int dH = ha[a] - hb[b];
+            Q[a][b] += (long long)dH * (long long)dH;
+            const float dl = la[a] - lb[b];
+            const float dx = xa[a] - xb[b];
+            W[a][b] = fmaf(fmaf(2.f, dx, -dl), dl, W[a][b]);
+          }
+      }
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const long long Qv = Q[a][b];
+          const long long qi = Qv >> (2 * G);
+          const int eint = qi > 1000 ? 1000 : (int)qi;
+          const int kidx = (int)(Qv >> sh) & mask_f;
+          const long long rem = Qv & mask_r;                       // < 2^(2G - 10) <= 2^46
+          const int ra = (int)(rem >> 23), rb = (int)(rem & 0x7FFFFF);
+          const float pa = __fmul_rn(__fsub_rn(__int_as_float(ra | 0x4B000000), 8388608.f), scaleA);  // exact
+          const float pb = __fmul_rn(__fsub_rn(__int_as_float(rb | 0x4B000000), 8388608.f), scaleB);  // exact
+          // (t_hi, t_lo) = pa + pb exactly (TwoSum), then r = t + W
+          const float t_hi = __fadd_rn(pa, pb);
+          const float tb = __fsub_rn(t_hi, pa);
+          const float t_lo = __fadd_rn(__fsub_rn(pa, __fsub_rn(t_hi, tb)), __fsub_rn(pb, tb));
+          const float w = W[a][b];
+          const float r_hi = __fadd_rn(t_hi, w);
+          const float bb = __fsub_rn(r_hi, t_hi);
+          const float r_lo = __fadd_rn(__fadd_rn(__fsub_rn(t_hi, __fsub_rn(r_hi, bb)), __fsub_rn(w, bb)), t_lo);
+          // x = r ln2 (double-float)
+          const float x_hi = __fmul_rn(r_hi, kLn2Hi);
+          float x_lo = fmaf(r_hi, kLn2Hi, -x_hi);
+          x_lo = fmaf(r_hi, kLn2Lo, x_lo);
+          x_lo = fmaf(r_lo, kLn2Hi, x_lo);
+          // e^-x = 1 - x + x^2 (1/2 - x/6 + x^2/24)
+          const float tail = __fmul_rn(__fmul_rn(x_hi, x_hi), fmaf(x_hi, fmaf(x_hi, 1.f / 24.f, -1.f / 6.f), 0.5f));
+          const float P_hi = __fsub_rn(1.f, x_hi);
+          const float P_lo = __fadd_rn(__fsub_rn(__fsub_rn(__fsub_rn(1.f, P_hi), x_hi), x_lo), tail);
+          const float2 T = tab[kidx];
+          float K_hi = __fmul_rn(T.x, P_hi);
+          float K_lo = fmaf(T.x, P_hi, -K_hi);
+          K_lo = fmaf(T.x, P_lo, K_lo);
+          K_lo = fmaf(T.y, P_hi, K_lo);
+          const float sc = (eint < 100) ? __int_as_float((127 - eint) << 23) : 0.f;
+          K_hi = __fmul_rn(K_hi, sc);
+          K_lo = __fmul_rn(K_lo, sc);
+          const float p_hi = __fmul_rn(K_hi, vh[b]);
+          float p_lo = fmaf(K_hi, vh[b], -p_hi);
+          p_lo = fmaf(K_hi, vl[b], p_lo);
+          p_lo = fmaf(K_lo, vh[b], p_lo);
+          const float sum = __fadd_rn(s_hi[a], p_hi);
+          const float bv = __fsub_rn(sum, s_hi[a]);
+          const float e2 = __fadd_rn(__fsub_rn(s_hi[a], __fsub_rn(sum, bv)), __fsub_rn(p_hi, bv));
+          s_hi[a] = sum;
+          s_lo[a] = __fadd_rn(s_lo[a], __fadd_rn(e2, p_lo));
+        }
+    }
+    __syncthreads();
+  }
+
+  double r8[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    double v = (double)s_hi[a] + (double)s_lo[a];
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    r8[a] = v;
+  }
+  __syncthreads();
+  const int wc = warp & 1;
+  if ((lane & 7) == 0) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) red[wc * kTile + ty * 8 + a] = r8[a];
+  }
+  __syncthreads();
+  if (tid < kTile) part[(size_t)split * ldn + row0 + tid] = red[tid] + red[kTile + tid];
+}
+
+static size_t rbf_emu_smem(int p) {
+  return (size_t)9 * p * kTile * 4 + (size_t)(1 << kTB) * sizeof(float2) + 2 * kTile * sizeof(double) +
+         4 * sizeof(uint64_t);
+}
+
 // RBF, FP64: entries exp(-gamma ||x_i - x_j||^2) from the centred FP64 copy.
 __global__ void __launch_bounds__(kThreads, 1)
     gram_rbf_high_kernel(const double* __restrict__ xc, const double* __restrict__ v, double* __restrict__ part,
@@ -369,6 +581,19 @@ cudaError_t gram_high(Handle* h, const double* V, double* U, int m, cudaStream_t
       gram_lap_high_kernel<<<dim3(row_tiles, splits), kThreads, smem, st>>>(
           h->tm_hq, h->tm_hl, vhl, h->exp_table, part, (int)h->p, (int)h->ldn, h->grid_G, tps, col_tiles,
           h->err_flag);
+      prof_mark(h, 1, false, st);
+      h->launches++;
+    } else if (h->hq) {
+      float2* vhl = reinterpret_cast<float2*>(h->v32);
+      split_hilo_kernel<<<grid_for(h->ldn), 256, 0, st>>>(vcol, vhl, h->n, h->ldn);
+      h->launches++;
+      const size_t smem = rbf_emu_smem((int)h->p);
+      e = cudaFuncSetAttribute(gram_rbf_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      prof_mark(h, 1, true, st);
+      gram_rbf_emu_kernel<<<dim3(row_tiles, splits), kThreads, smem, st>>>(
+          h->tm_hq, h->tm_hl, h->tm_xs32, vhl, h->exp_table, part, (int)h->p, (int)h->ldn, h->grid_G, tps,
+          col_tiles, h->err_flag);
       prof_mark(h, 1, false, st);
       h->launches++;
     } else {

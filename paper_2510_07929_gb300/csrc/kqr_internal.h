@@ -19,6 +19,7 @@ constexpr int kThreads = 256;
 constexpr int kMaxP = 64;          // features supported by the tile kernels
 constexpr int kMaxRhs = 8;         // right-hand sides of one Gram product
 constexpr int kExpTableBits = 10;  // 2^-f table of the double-float exp2
+constexpr int kRbfEmuMaxP = 40;    // features of the fixed-point FP64-class RBF product
 
 // Status values a kernel writes to the device error word.
 constexpr int kErrWaitTimeout = 1;

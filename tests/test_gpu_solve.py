@@ -77,6 +77,18 @@ def test_mixed_precision_solve_matches_oracle(K_, name, n):
     check_against_oracle(wl, alpha, beta, v, z, kkt)
 
 
+@pytest.mark.parametrize("lam", [1e-2, 3e-2])
+def test_low_rank_rbf_solve_survives_rounding_curvature(K_, lam):
+    """The p = 2 generator of Sec. 4.1 with the RBF kernel (gamma = 0.1) at the
+    small end of the paper's lambda range: K is numerically low-rank, so FP32 CG
+    meets non-positive curvatures in directions below its accuracy.  The solve
+    truncates those CG runs and must still meet the parity contract."""
+    wl = W.yuan2006(n=2000, gamma=0.1, tau=0.5, lam=lam)
+    alpha, beta, v, z, kkt, info = gpu_solve(K_, wl, tol=1e-7)
+    assert info["status"] == K_.OK
+    check_against_oracle(wl, alpha, beta, v, z, kkt)
+
+
 @pytest.mark.parametrize("precond", [1, 2])
 def test_paper_preconditioner_and_plain_cg_converge(K_, precond):
     wl = W.rbf_small(n=900, seed=5)
