@@ -147,6 +147,29 @@ def oracle_matvec_seconds(wl, rows: int = 96, seed: int = 0):
     return dt * wl.n / idx.size, idx.size, dt
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (the job finishes when every replica has)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput_value(total_ms: float, world: int, steps: int) -> float:
+    """Seconds per solve over the whole job: every rank solves one replica per step."""
+    return total_ms / 1e3 / (world * steps)
+
+
+def bench_config(wl, args, world: int) -> dict:
+    """The bench line's config, shared by both arms."""
+    return {"workload": describe(wl, args), "n": wl.n, "p": wl.p, "kernel": wl.kind, "rank0": args.rank0,
+            "xi": 1e-6, "preconditioner": "RPCholesky + floored residual diagonal (Woodbury)",
+            "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1gpu"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -165,7 +188,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": describe(wl, args)},
+            "config": bench_config(wl, args, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -248,13 +271,9 @@ def run_ours(args):
     n32, ms32 = prob.profile_read(0)
     nhp, mshp = prob.profile_read(1)
     prob.profile(False)
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     units = world * args.steps
-    value = total_ms / 1e3 / units                    # seconds per solve, whole job
+    value = job_throughput_value(total_ms, world, args.steps)
 
     # e2e through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -274,11 +293,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             e2e_s.append(time.perf_counter() - t0)
         barrier()
-        tot = sum(e2e_s)
-        if dist is not None:
-            t = torch.tensor([tot], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(sum(e2e_s), dist, "cuda")
         e2e = {"value": tot / units, "unit": "s", "h2d_bytes_per_step": int(wl.X.nbytes + wl.y.nbytes),
                "d2h_bytes_per_step": int(wl.n * 8 + 16)}
 
@@ -310,9 +325,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32,f64", "data": "synthetic",
-            "config": {"workload": describe(wl, args), "n": n, "p": p, "kernel": wl.kind, "rank0": args.rank0,
-                       "xi": 1e-6, "preconditioner": "RPCholesky + floored residual diagonal (Woodbury)",
-                       "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1gpu"},
+            "config": bench_config(wl, args, world),
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
             "high_precision_gram": hp,
             "solve": {"kkt": max(kkts), "phase1_iters": last["phase1_iters"], "alm_iters": last["phase2_iters"],
