@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--path-lambdas", type=int, default=50)
     ap.add_argument("--path-precond", type=int, default=0, help="0 Nystrom+diag, 1 paper, 2 none (NALM)")
     ap.add_argument("--prec-taus", default="0.5", help="comma-separated tau values for --mode precision")
+    ap.add_argument("--batch-p-in-smem", action="store_true",
+                    help="--mode batch: stage the Gram tile through shared memory instead of tensor memory")
     ap.add_argument("--time-limit", type=float, default=600.0, help="per-solve wall-clock limit (s) in the study modes")
     return ap.parse_args()
 
@@ -563,7 +565,7 @@ def run_batch(args):
         pass
     bf16 = peaks.get("bf16_tflops", 1900.0)
     peak = bf16 * 1.1 / 2.25
-    with kqr.Batch(Xs, 0.125) as bt:
+    with kqr.Batch(Xs, 0.125, p_in_smem=args.batch_p_in_smem) as bt:
         stream = torch.cuda.Stream()
         bt.set_stream(stream)
         Vd = torch.tensor(V, device="cuda")
@@ -600,6 +602,7 @@ def run_batch(args):
     kern_ms = ms_k / max(nk, 1)
     flops = entries * (2 * 8 + 2 * 64)
     out = {"mode": "batch", "workload": "64 RBF problems, n_b ~ U{1000..20000} (seed 0), p=8, gamma=1/8, m=64",
+           "gram_tile": "shared memory" if args.batch_p_in_smem else "tensor memory",
            "sum_n": int(sum(sizes)), "entries": entries, "ms_per_product": ms, "kernel_ms": kern_ms,
            "tflops": flops / (kern_ms * 1e-3) / 1e12,
            "roofline": {"bound": "tensor", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": peak,

@@ -299,10 +299,13 @@ kqr_status kqr_heldout_grad(kqr_handle* h, const double* X, const double* Xh, co
  * kqr_set_stream, kqr_profile(_read) with kernel id 0, kqr_launch_count,
  * kqr_last_error and kqr_destroy apply).  X: host, offsets[B] x p row-major;
  * offsets: host, B + 1 entries, offsets[0] = 0, strictly increasing;
- * p in [1, 32]; gammas: host, B positive values.  The handle owns device
- * copies; the caller keeps its arrays.  Synchronises. */
+ * p in [1, 32]; gammas: host, B positive values; flags: 0, or
+ * KQR_BATCH_P_IN_SMEM to stage each Gram tile through shared memory instead of
+ * tensor memory (the same values; a layout choice kept for comparison).  The
+ * handle owns device copies; the caller keeps its arrays.  Synchronises. */
+#define KQR_BATCH_P_IN_SMEM 1
 kqr_status kqr_batch_create(const double* X, const int64_t* offsets, int64_t B, int64_t p, const double* gammas,
-                            kqr_handle** out);
+                            int32_t flags, kqr_handle** out);
 
 /* U = blockdiag(K_1 .. K_B) V for V (offsets[B] x m, row-major, rows ordered as
  * X) with m in [1, 64]; U has the same layout.  Host pointers; allocates

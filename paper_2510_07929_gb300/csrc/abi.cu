@@ -616,7 +616,7 @@ kqr_status kqr_refactor(kqr_handle* kh, const double* pivot_uniforms) {
 }
 
 kqr_status kqr_batch_create(const double* X, const int64_t* offsets, int64_t B, int64_t p, const double* gammas,
-                            kqr_handle** out) {
+                            int32_t flags, kqr_handle** out) {
   if (!out) return KQR_INVALID_ARG;
   *out = nullptr;
   kqr_handle* kh = new (std::nothrow) kqr_handle();
@@ -634,7 +634,7 @@ kqr_status kqr_batch_create(const double* X, const int64_t* offsets, int64_t B, 
   h->err_flag = (int*)dev_alloc(h, 64);
   if (!h->err_flag) return fail(h, KQR_OOM, "error flag");
   if ((e = cudaMemsetAsync(h->err_flag, 0, 64, h->stream)) != cudaSuccess) return cuda_fail(h, e, "error flag");
-  kqr_status s = batch_create(h, X, offsets, B, p, gammas);
+  kqr_status s = batch_create(h, X, offsets, B, p, gammas, flags);
   if (s != KQR_OK) return s;
   h->n = offsets[B];
   h->p = p;

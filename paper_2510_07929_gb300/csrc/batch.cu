@@ -7,7 +7,8 @@
 // Both contractions run on the tcgen05 tensor cores (kind::tf32, FP32
 // accumulation in tensor memory):
 //   S = XS_I XS_J^T        (128 x 64 tile, K = p, from TMA tiles, 128-byte swizzle)
-//   P = exp2(2 S - n_i - n_j) = K_IJ   (epilogue warps: TMEM -> registers -> shared)
+//   P = exp2(2 S - n_i - n_j) = K_IJ   (epilogue warps: TMEM -> registers -> TMEM, or
+//                                        shared memory with KQR_BATCH_P_IN_SMEM)
 //   U_I += P V_J           (128 x 64 accumulator, K = 64 Gram columns)
 // with XS = sqrt(gamma log2 e)(x - mean_b) rounded to TF32 and n = |XS|^2 of
 // the rounded rows (so the tile is the RBF kernel at those rows, and stays
@@ -58,6 +59,7 @@ constexpr uint32_t kOffBar = kOffP + 2 * kPBytes;
 constexpr int kNumBars = 2 + 2 + 2 * kXStages + 2 * kVStages + 2 * kSBufs + 2 + 2 + 2 + 2 + 1;
 constexpr size_t kBatchSmem = 1024 + kOffBar + kNumBars * 8 + 16;
 constexpr uint32_t kUCol = 64 * kSBufs;     // first TMEM column of the U accumulators
+constexpr uint32_t kPCol = kUCol + 128;     // first TMEM column of the P tiles (P kept in tensor memory)
 
 __device__ __forceinline__ void tmem_alloc_b(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
@@ -85,6 +87,31 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+// D[tmem] (+)= A[tmem] B[smem]^T, tf32, A held in tensor memory (row i in lane i, K along columns).
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 32 consecutive 32-bit columns of this thread's TMEM lane, then wait for the stores.
+__device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+      "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+      "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+      "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -149,6 +176,7 @@ struct MmaStep {
 
 // items[i] = {row0 (padded row of the tile), col0 (padded first row of its problem),
 //             nt (64-column steps), nvalid (rows < n_b in the tile)}; out0[i] = output row of row0.
+template <bool PT>
 __global__ void __launch_bounds__(kBatchThreads, 1)
     batch_kv_kernel(const __grid_constant__ CUtensorMap tm_xi, const __grid_constant__ CUtensorMap tm_xj,
                     const __grid_constant__ CUtensorMap tm_v, const float* __restrict__ nrm,
@@ -267,8 +295,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
 #pragma unroll
         for (int k = 0; k < kBN / 8; ++k) {
           const uint32_t ka = (uint32_t)(k >> 2), kb = (uint32_t)(k & 3) * 32u;
-          mma_tf32(d, desc_sw128(pa + ka * kPAtom + kb), desc_sw128(va + ka * kVAtom + kb), idesc,
-                   (ps.first && k == 0) ? 0u : 1u);
+          if (PT)
+            mma_tf32_ta(d, tmem + kPCol + (uint32_t)(pb * 64 + k * 8), desc_sw128(va + ka * kVAtom + kb), idesc,
+                        (ps.first && k == 0) ? 0u : 1u);
+          else
+            mma_tf32(d, desc_sw128(pa + ka * kPAtom + kb), desc_sw128(va + ka * kVAtom + kb), idesc,
+                     (ps.first && k == 0) ? 0u : 1u);
         }
         mma_commit(&p_empty[pb]);
         mma_commit(&vl_empty[ps.stage]);
@@ -352,13 +384,19 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
           ok = false;
           break;
         }
-        // columns [32 ch, 32 ch + 32) are swizzle atom ch of the P tile
-        unsigned char* prow = base + kOffP + pb * kPBytes + ch * kPAtom + r * 128;
+        if (PT) {
+          // P tile in tensor memory, lane = row, columns [32 ch, 32 ch + 32)
+          tmem_store32(tmem + kPCol + (uint32_t)(pb * 64 + ch * 32) + lane_off, e);
+          fence_before();
+        } else {
+          // columns [32 ch, 32 ch + 32) are swizzle atom ch of the P tile in shared memory
+          unsigned char* prow = base + kOffP + pb * kPBytes + ch * kPAtom + r * 128;
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          *reinterpret_cast<uint4*>(prow + ((c ^ (r & 7)) * 16)) =
-              make_uint4(e[4 * c], e[4 * c + 1], e[4 * c + 2], e[4 * c + 3]);
-        fence_async_smem();
+          for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<uint4*>(prow + ((c ^ (r & 7)) * 16)) =
+                make_uint4(e[4 * c], e[4 * c + 1], e[4 * c + 2], e[4 * c + 3]);
+          fence_async_smem();
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive_1(&p_full[pb]);
       }
@@ -448,7 +486,7 @@ bool make_tmap_2d_f32_sw128(CUtensorMap* tm, void* base, int64_t inner, int64_t 
                             int box_inner, int box_outer);
 
 kqr_status batch_create(Handle* h, const double* X, const int64_t* offsets, int64_t B, int64_t p,
-                        const double* gammas) {
+                        const double* gammas, int32_t flags) {
   if (!X || !offsets || !gammas) return fail(h, KQR_INVALID_ARG, "X, offsets and gammas must be non-null");
   if (B < 1 || B > (1 << 24)) return fail(h, KQR_INVALID_ARG, "B must be in [1, 2^24]");
   if (p < 1 || p > 32) return fail(h, KQR_INVALID_ARG, "batched products take p in [1, 32]");
@@ -461,8 +499,10 @@ kqr_status batch_create(Handle* h, const double* X, const int64_t* offsets, int6
   if (N > ((int64_t)1 << 30)) return fail(h, KQR_INVALID_ARG, "too many rows in total");
   for (int64_t i = 0; i < N * p; ++i)
     if (!std::isfinite(X[i])) return fail(h, KQR_INVALID_ARG, "X has a non-finite entry");
+  if (flags & ~KQR_BATCH_P_IN_SMEM) return fail(h, KQR_INVALID_ARG, "unknown batch flags");
   BatchData* bd = new BatchData();
   h->batch = bd;
+  bd->p_in_smem = (flags & KQR_BATCH_P_IN_SMEM) != 0;
   bd->B = B;
   bd->p = p;
   bd->off.assign(offsets, offsets + B + 1);
@@ -561,14 +601,15 @@ cudaError_t batch_kmatmul(Handle* h, const double* V, double* U, int m, cudaStre
   h->launches++;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(batch_kv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
+  auto kern = bd->p_in_smem ? batch_kv_kernel<false> : batch_kv_kernel<true>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
   if (e != cudaSuccess) return e;
   const int grid = std::min(h->num_sms, bd->n_items);
   const int ksteps = (int)((bd->p + 7) / 8);
   prof_mark(h, 0, true, st);
-  batch_kv_kernel<<<grid, kBatchThreads, kBatchSmem, st>>>(bd->tm_xi, bd->tm_xj, bd->tm_v, bd->nrm,
-                                                 reinterpret_cast<const int4*>(bd->items), bd->out0, bd->n_items,
-                                                 ksteps, U, m, h->err_flag);
+  kern<<<grid, kBatchThreads, kBatchSmem, st>>>(bd->tm_xi, bd->tm_xj, bd->tm_v, bd->nrm,
+                                              reinterpret_cast<const int4*>(bd->items), bd->out0, bd->n_items,
+                                              ksteps, U, m, h->err_flag);
   prof_mark(h, 0, false, st);
   h->launches++;
   return cudaGetLastError();

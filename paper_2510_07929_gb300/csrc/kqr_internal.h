@@ -240,9 +240,10 @@ struct BatchData {
   int64_t* d_off = nullptr;
   int64_t* d_roff = nullptr;
   CUtensorMap tm_xi, tm_xj, tm_v;
+  bool p_in_smem = false;               // stage the Gram tile through shared memory, not TMEM
 };
 kqr_status batch_create(Handle* h, const double* X, const int64_t* offsets, int64_t B, int64_t p,
-                        const double* gammas);
+                        const double* gammas, int32_t flags);
 cudaError_t batch_kmatmul(Handle* h, const double* V, double* U, int m, cudaStream_t st);
 void batch_free(Handle* h);
 #define KQR_SINGLE(h)                                                                          \

@@ -82,7 +82,7 @@ SIGNATURES = {
                                       ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "kqr_refactor": (ctypes.c_int, [_P, _DP]),
     "kqr_heldout_grad": (ctypes.c_int, [_P, _DP, _DP, _DP, _I64, _DP, _DP, _DP, _DP]),
-    "kqr_batch_create": (ctypes.c_int, [_DP, ctypes.POINTER(_I64), _I64, _I64, _DP, ctypes.POINTER(_P)]),
+    "kqr_batch_create": (ctypes.c_int, [_DP, ctypes.POINTER(_I64), _I64, _I64, _DP, _I32, ctypes.POINTER(_P)]),
     "kqr_batch_kmatmul": (ctypes.c_int, [_P, _DP, _DP, _I64]),
     "kqr_batch_kmatmul_dev": (ctypes.c_int, [_P, _P, _P, _I64]),
     "kqr_profile": (ctypes.c_int, [_P, _I32]),
@@ -312,7 +312,7 @@ class Batch:
     """B independent RBF problems (X_b n_b x p, gamma_b) for batched products
     U_b = K_b V_b with up to 64 right-hand sides (kqr_batch_create)."""
 
-    def __init__(self, Xs, gammas):
+    def __init__(self, Xs, gammas, p_in_smem: bool = False):
         self._lib = lib()
         self.sizes = [int(x.shape[0]) for x in Xs]
         self.p = int(Xs[0].shape[1])
@@ -321,7 +321,7 @@ class Batch:
         self.gammas = np.ascontiguousarray(np.broadcast_to(np.asarray(gammas, dtype=np.float64), (len(Xs),)))
         h = ctypes.c_void_p()
         st = self._lib.kqr_batch_create(_dptr(self.X), self.offsets.ctypes.data_as(ctypes.POINTER(_I64)), len(Xs),
-                                        self.p, _dptr(self.gammas), ctypes.byref(h))
+                                        self.p, _dptr(self.gammas), 1 if p_in_smem else 0, ctypes.byref(h))
         self._h = h
         if st != OK:
             msg = self._lib.kqr_last_error(h).decode() if h.value else ""

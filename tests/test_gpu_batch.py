@@ -51,12 +51,14 @@ def _check(Xs, gammas, V, U, rows=None):
     return worst
 
 
+@pytest.mark.parametrize("p_in_smem", [False, True])
 @pytest.mark.parametrize("sizes,p,m", [([1, 63, 129, 300, 517], 8, 64), ([130, 64, 65], 3, 7),
                                        ([700, 256], 20, 1), ([2, 1000], 32, 33)])
-def test_batch_products_match_oracle(K_, sizes, p, m):
+def test_batch_products_match_oracle(K_, sizes, p, m, p_in_smem):
+    """Gram tile kept in tensor memory (default) or staged through shared memory."""
     Xs, gammas = _batch(sizes, p, seed=len(sizes) * 100 + p)
     V = np.random.default_rng(p).standard_normal((sum(sizes), m))
-    with K_.Batch(Xs, gammas) as bt:
+    with K_.Batch(Xs, gammas, p_in_smem=p_in_smem) as bt:
         U = bt.kmatmul(V)
         assert bt.launches >= 2
     _check(Xs, gammas, V, U)
