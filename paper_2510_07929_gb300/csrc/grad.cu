@@ -202,7 +202,9 @@ extern "C" kqr_status kqr_heldout_grad(kqr_handle* kh, const double* X, const do
   uo.rank0 = 2;
   uo.adaptive_rank = 0;
   uo.precond = KQR_PRECOND_NONE;
-  uo.rbf_tensor_cores = h->opt.rbf_tensor_cores;
+  // CUDA-core FP32 products: the coordinate-weighted sums below cancel in x_k (K b)_k -
+  // (K x b)_k, where the three-TF32 tensor-core form (~2^-21 relative) loses a digit.
+  uo.rbf_tensor_cores = 0;
   kqr_handle* ukh = nullptr;
   kqr_status s = kqr_create(Xu.data(), yu.data(), N, p, KQR_RBF, gamma, &uo, &ukh);
   if (s != KQR_OK) {
