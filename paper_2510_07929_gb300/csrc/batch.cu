@@ -18,8 +18,8 @@
 // through TMA rings of 4 and 5 stages.  Items are sorted by length and dealt
 // round-robin to one persistent CTA per SM.  Warp roles (320 threads): warp 0
 // issues TMA copies, warp 1 owns tensor memory and issues the MMAs, warps 2-9
-// are the epilogue (thread = TMEM lane = row; two warps per lane group split the
-// 64 columns).  Tensor memory: four S buffers and two U accumulators (64 columns
+// are the epilogue in two groups of four that take alternate steps (thread =
+// TMEM lane = row), so two tiles are exponentiated at once.  Tensor memory: four S buffers and two U accumulators (64 columns
 // each); the first MMAs run two steps ahead of the second ones, so the epilogue
 // finds its next S tile computed, and the read-out of item i overlaps item i + 1.
 // Every wait is bounded; a timeout sets the error flag and an abort flag that
@@ -43,18 +43,20 @@ constexpr int kXStages = 4;                 // X_J ring (released after the firs
 constexpr int kVStages = 5;                 // V_J ring (released after the second MMA)
 constexpr int kSBufs = 4;                   // S tiles in tensor memory
 constexpr int kLookahead = 2;               // first MMAs issued ahead of the second ones
-constexpr int kEpiWarps = 8;                // two per SM sub-partition, 32 columns each
+constexpr int kEpiWarps = 8;                // two groups of four, alternate steps
 constexpr int kBatchThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kXIBytes = kBM * 128;    // 128 rows x 128 B (32 TF32 features, zero padded)
 constexpr uint32_t kXJBytes = kBN * 128;    // 64 rows x 128 B
 constexpr uint32_t kVAtom = kBR * 128;      // 64 right-hand sides x 32 columns
-constexpr uint32_t kVBytes = 2 * kVAtom;
+constexpr uint32_t kVBytes = 2 * kVAtom;      // bytes the TMA copies of V_J bring
+constexpr uint32_t kNrmBytes = kBN * 4;       // the 64 column norms of the step (bulk copy)
+constexpr uint32_t kVStride = kVBytes + 1024; // V_J atoms, then the norms (keeps 1024-byte alignment)
 constexpr uint32_t kPAtom = kBM * 128;      // 128 rows x 32 columns
 constexpr uint32_t kPBytes = 2 * kPAtom;
 constexpr uint32_t kOffXI = 0;
 constexpr uint32_t kOffXJ = kOffXI + 2 * kXIBytes;
 constexpr uint32_t kOffV = kOffXJ + kXStages * kXJBytes;
-constexpr uint32_t kOffP = kOffV + kVStages * kVBytes;
+constexpr uint32_t kOffP = kOffV + kVStages * kVStride;
 constexpr uint32_t kOffBar = kOffP + 2 * kPBytes;
 constexpr int kNumBars = 2 + 2 + 2 * kXStages + 2 * kVStages + 2 * kSBufs + 2 + 2 + 2 + 2 + 1;
 constexpr size_t kBatchSmem = 1024 + kOffBar + kNumBars * 8 + 16;
@@ -112,6 +114,14 @@ __device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t* v) 
       "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
       : "memory");
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -212,14 +222,14 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     for (int i = 0; i < 2; ++i) {
       mbar_init(&xi_full[i], 1);
       mbar_init(&xi_empty[i], 1);
-      mbar_init(&p_full[i], kEpiWarps);
+      mbar_init(&p_full[i], kEpiWarps / 2);
       mbar_init(&p_empty[i], 1);
       mbar_init(&u_full[i], 1);
-      mbar_init(&u_empty[i], kEpiWarps);
+      mbar_init(&u_empty[i], kEpiWarps / 2);
     }
     for (int i = 0; i < kSBufs; ++i) {
       mbar_init(&s_full[i], 1);
-      mbar_init(&s_empty[i], kEpiWarps);
+      mbar_init(&s_empty[i], kEpiWarps / 2);
     }
     for (int i = 0; i < kXStages; ++i) {
       mbar_init(&xl_full[i], 1);
@@ -266,9 +276,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
             ++q;                         // the X_J copy of this step is in flight
             break;
           }
-          mbar_arrive_expect_tx(&vl_full[vs], kVBytes);
-          tma_load_2d(base + kOffV + vs * kVBytes, &tm_v, c0, 0, &vl_full[vs]);
-          tma_load_2d(base + kOffV + vs * kVBytes + kVAtom, &tm_v, c0 + 32, 0, &vl_full[vs]);
+          mbar_arrive_expect_tx(&vl_full[vs], kVBytes + kNrmBytes);
+          tma_load_2d(base + kOffV + vs * kVStride, &tm_v, c0, 0, &vl_full[vs]);
+          tma_load_2d(base + kOffV + vs * kVStride + kVAtom, &tm_v, c0 + 32, 0, &vl_full[vs]);
+          bulk_load(base + kOffV + vs * kVStride + kVBytes, nrm + c0, kNrmBytes, &vl_full[vs]);
           ++q;
         }
       }
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
         fence_after();
         const uint32_t d = tmem + kUCol + (uint32_t)(ps.ub * 64);
         const uint32_t pa = sbase + kOffP + pb * kPBytes;
-        const uint32_t va = sbase + kOffV + ps.stage * kVBytes;
+        const uint32_t va = sbase + kOffV + ps.stage * kVStride;
 #pragma unroll
         for (int k = 0; k < kBN / 8; ++k) {
           const uint32_t ka = (uint32_t)(k >> 2), kb = (uint32_t)(k & 3) * 32u;
@@ -347,9 +358,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       dwait(drain, 0);
     }
   } else {
-    // ---- epilogue: thread = TMEM lane = row of the item; warp half ch owns columns [32 ch, 32 ch + 32) ----
+    // ---- epilogue: two groups of four warps take alternate steps (group g the steps
+    // q with q mod 2 = g), so two Gram tiles are exponentiated at once; in a group,
+    // thread = TMEM lane = row, and each warp covers all 64 columns in two halves.
     const int lg = warp & 3;                  // TMEM lane group this warp may access
-    const int ch = (warp - 2) >> 2;           // column half
+    const int grp = (warp - 2) >> 2;
     const int r = lg * 32 + lane;
     const uint32_t lane_off = (uint32_t)(lg * 32) << 16;
     int q = 0, seq = 0;
@@ -357,65 +370,72 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++seq) {
       const int4 I = items[it];
       const float ni = __ldg(nrm + I.x + r);
+      const int q_last = q + I.z - 1;
       for (int j = 0; j < I.z; ++j, ++q) {
-        const int sb = q % kSBufs;
-        if (!bwait(&s_full[sb], (q / kSBufs) & 1, abort_flag, err)) {
+        if ((q & 1) != grp) continue;
+        const int sb = q % kSBufs, vs = q % kVStages, pb = q & 1;
+        if (!bwait(&s_full[sb], (q / kSBufs) & 1, abort_flag, err) ||
+            !bwait(&vl_full[vs], (q / kVStages) & 1, abort_flag, err) ||
+            !bwait(&p_empty[pb], ((q >> 1) & 1) ^ 1, abort_flag, err)) {
           ok = false;
           break;
         }
         fence_after();
-        float g[32];
-        tmem_load32(tmem + (uint32_t)(sb * 64 + ch * 32) + lane_off, g);
+        // the step's column norms arrived with V_J (the stage stays until this step's second MMA)
+        const float4* nj4 = reinterpret_cast<const float4*>(base + kOffV + vs * kVStride + kVBytes);
+#pragma unroll 1
+        for (int ch = 0; ch < 2; ++ch) {
+          float g[32];
+          tmem_load32(tmem + (uint32_t)(sb * 64 + ch * 32) + lane_off, g);
+          uint32_t e[32];
+#pragma unroll
+          for (int c4 = 0; c4 < 8; ++c4) {
+            const float4 nn = nj4[ch * 8 + c4];
+            e[4 * c4 + 0] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 0], -(ni + nn.x))));
+            e[4 * c4 + 1] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 1], -(ni + nn.y))));
+            e[4 * c4 + 2] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 2], -(ni + nn.z))));
+            e[4 * c4 + 3] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 3], -(ni + nn.w))));
+          }
+          if (PT) {
+            // P tile in tensor memory, lane = row, columns [32 ch, 32 ch + 32)
+            tmem_store32(tmem + kPCol + (uint32_t)(pb * 64 + ch * 32) + lane_off, e);
+          } else {
+            // columns [32 ch, 32 ch + 32) are swizzle atom ch of the P tile in shared memory
+            unsigned char* prow = base + kOffP + pb * kPBytes + ch * kPAtom + r * 128;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              *reinterpret_cast<uint4*>(prow + ((c ^ (r & 7)) * 16)) =
+                  make_uint4(e[4 * c], e[4 * c + 1], e[4 * c + 2], e[4 * c + 3]);
+          }
+        }
         fence_before();
+        if (!PT) fence_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive_1(&s_empty[sb]);
-        const float4* nj4 = reinterpret_cast<const float4*>(nrm + I.y + j * kBN + ch * 32);
-        uint32_t e[32];
-#pragma unroll
-        for (int c4 = 0; c4 < 8; ++c4) {
-          const float4 nn = __ldg(nj4 + c4);
-          e[4 * c4 + 0] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 0], -(ni + nn.x))));
-          e[4 * c4 + 1] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 1], -(ni + nn.y))));
-          e[4 * c4 + 2] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 2], -(ni + nn.z))));
-          e[4 * c4 + 3] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 3], -(ni + nn.w))));
+        if (lane == 0) {
+          mbar_arrive_1(&s_empty[sb]);
+          mbar_arrive_1(&p_full[pb]);
         }
-        const int pb = q & 1;
-        if (!bwait(&p_empty[pb], ((q >> 1) & 1) ^ 1, abort_flag, err)) {
-          ok = false;
-          break;
-        }
-        if (PT) {
-          // P tile in tensor memory, lane = row, columns [32 ch, 32 ch + 32)
-          tmem_store32(tmem + kPCol + (uint32_t)(pb * 64 + ch * 32) + lane_off, e);
-          fence_before();
-        } else {
-          // columns [32 ch, 32 ch + 32) are swizzle atom ch of the P tile in shared memory
-          unsigned char* prow = base + kOffP + pb * kPBytes + ch * kPAtom + r * 128;
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            *reinterpret_cast<uint4*>(prow + ((c ^ (r & 7)) * 16)) =
-                make_uint4(e[4 * c], e[4 * c + 1], e[4 * c + 2], e[4 * c + 3]);
-          fence_async_smem();
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive_1(&p_full[pb]);
       }
       if (!ok) break;
+      if ((q_last & 1) != grp) continue;        // the other group reads this item's result
       const int ub = seq & 1;
       if (!bwait(&u_full[ub], (seq >> 1) & 1, abort_flag, err)) break;
       fence_after();
-      float u[32];
-      tmem_load32(tmem + kUCol + (uint32_t)(ub * 64 + ch * 32) + lane_off, u);
+#pragma unroll 1
+      for (int ch = 0; ch < 2; ++ch) {
+        float u[32];
+        tmem_load32(tmem + kUCol + (uint32_t)(ub * 64 + ch * 32) + lane_off, u);
+        if (r < I.w) {
+          double* o = out + (size_t)(out0[it] + r) * m + ch * 32;
+          const int mc = m - ch * 32;
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (c < mc) o[c] = (double)u[c];
+        }
+      }
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_1(&u_empty[ub]);
-      if (r < I.w) {
-        double* o = out + (size_t)(out0[it] + r) * m + ch * 32;
-        const int mc = m - ch * 32;
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (c < mc) o[c] = (double)u[c];
-      }
     }
   }
   fence_before();
