@@ -10,7 +10,8 @@
 // For the held-out loss l = sum_h rho_tau(y_h - f_h) with g_h = d rho / d f_h,
 // let a = [(K_{E,h} g) / lambda ; sum_h g_h] and solve
 //   [K_EE / lambda, 1; 1^T, 0] [u; w] = a
-// (two CG solves with K_EE, on the training problem's preconditioner); then
+// (two CG solves with K_EE, FP64-class products, on the training problem's
+// preconditioner); then
 //   dl/dtheta = g^T (d f_h / d theta)|_{alpha,beta} - u^T (d F_E / d theta)|_{alpha,beta}.
 // Every Gram-weighted sum the partial derivatives need is a product of the
 // tiled Gram kernels with one of the vectors
@@ -178,6 +179,88 @@ __global__ void dx_kernel(const double* __restrict__ alpha, const double* __rest
   }
 }
 
+// Ap = K p + gam (1^T p) 1 + L o p, with K p from the FP64-class product.
+__global__ void adj_op_kernel(double* __restrict__ Ap, const double* __restrict__ Kp, const double* __restrict__ p,
+                              const double* __restrict__ L, const double* __restrict__ sump, double gam, int64_t n) {
+  const double sg = gam * (*sump);
+  GRID_LOOP(i, n) Ap[i] = Kp[i] + sg + L[i] * p[i];
+}
+
+__global__ void adj_step_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                                const double* __restrict__ Ap, double a, int64_t n) {
+  GRID_LOOP(i, n) {
+    x[i] += a * p[i];
+    r[i] -= a * Ap[i];
+  }
+}
+
+__global__ void adj_dir_kernel(double* __restrict__ p, const double* __restrict__ z, double b, int64_t n) {
+  GRID_LOOP(i, n) p[i] = z[i] + b * p[i];
+}
+
+// PCG on (K + gam 1 1^T + diag(L)) x = b with FP64-class Gram products and the problem's
+// Woodbury preconditioner (built for Lpre).  The adjoint system is as ill-conditioned as
+// K on the elbow set, where FP32 products would cap the gradient's accuracy.  dsc: 4
+// device doubles of scratch.
+static kqr_status adjoint_cg(Handle* h, const double* L, const double* Lpre, double gam, const double* b, double* x,
+                             double tol, int maxit, double* dsc, cudaStream_t st) {
+  const int64_t n = h->n;
+  double* r = vec(h, V_R);
+  double* z = vec(h, V_ZZ);
+  double* p = vec(h, V_P);
+  double* Kp = vec(h, V_KP);
+  double* Ap = vec(h, V_AP);
+  double hs[4];
+  auto get = [&](int k) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(hs + k, dsc + k, sizeof(double), cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+  };
+#define AK(call)                                              \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, #call);    \
+  } while (0)
+  AK(vec_fill(h, x, 0.0, n, st));
+  AK(vec_copy(h, r, b, n, st));
+  RedArgs rn;
+  rn.a = r;
+  AK(reduce(h, RED_NORM2, rn, n, dsc + 0, st));
+  AK(get(0));
+  if (std::sqrt(hs[0]) <= tol) return KQR_OK;
+  AK(precond_apply(h, Lpre, r, z, dsc + 1, st));
+  AK(get(1));
+  double rz = hs[1];
+  AK(vec_copy(h, p, z, n, st));
+  for (int it = 0; it < maxit; ++it) {
+    RedArgs rs;
+    rs.a = p;
+    AK(reduce(h, RED_SUM, rs, n, dsc + 2, st));
+    AK(gram_high(h, p, Kp, 1, st));
+    adj_op_kernel<<<grid_for(n), 256, 0, st>>>(Ap, Kp, p, L, dsc + 2, gam, n);
+    AK(cudaGetLastError());
+    RedArgs rd;
+    rd.a = p;
+    rd.b = Ap;
+    AK(reduce(h, RED_DOT, rd, n, dsc + 3, st));
+    AK(get(3));
+    const double pAp = hs[3];
+    if (!std::isfinite(pAp)) return fail(h, KQR_BREAKDOWN, "adjoint CG: non-finite curvature");
+    if (!(pAp > 0.0)) break;
+    adj_step_kernel<<<grid_for(n), 256, 0, st>>>(x, r, p, Ap, rz / pAp, n);
+    AK(cudaGetLastError());
+    AK(reduce(h, RED_NORM2, rn, n, dsc + 0, st));
+    AK(get(0));
+    if (std::sqrt(hs[0]) <= tol) break;
+    AK(precond_apply(h, Lpre, r, z, dsc + 1, st));
+    AK(get(1));
+    adj_dir_kernel<<<grid_for(n), 256, 0, st>>>(p, z, hs[1] / rz, n);
+    AK(cudaGetLastError());
+    rz = hs[1];
+  }
+#undef AK
+  return KQR_OK;
+}
+
 }  // namespace kqr
 
 using namespace kqr;
@@ -276,7 +359,6 @@ extern "C" kqr_status kqr_heldout_grad(kqr_handle* kh, const double* X, const do
   GK(cudaMemcpyAsync(hs.data(), sums, sizeof(double) * 16, cudaMemcpyDeviceToHost, st));
   GK(cudaStreamSynchronize(st));
   const double loss_v = hs[0], gsum = hs[1], nE = hs[2];
-  int its = 0;
   if (nE > 0) {
     RedArgs rn;
     rn.a = rhs1;
@@ -284,9 +366,9 @@ extern "C" kqr_status kqr_heldout_grad(kqr_handle* kh, const double* X, const do
     GK(cudaMemcpyAsync(h->scal_host + S_RED0 + 15, h->scal + S_RED0 + 15, sizeof(double), cudaMemcpyDeviceToHost, st));
     GK(cudaStreamSynchronize(st));
     const double nb1 = std::sqrt(h->scal_host[S_RED0 + 15]);
-    s = pcg(h, Ld, Lp, gam, rhs1, s1, nullptr, false, std::fmax(1e-300, 1e-8 * nb1), 2000, &its, st);
+    s = adjoint_cg(h, Ld, Lp, gam, rhs1, s1, std::fmax(1e-300, 1e-11 * nb1), 3000, sums + 12, st);
     if (s != KQR_OK) return done(s);
-    s = pcg(h, Ld, Lp, gam, rhs2, s2, nullptr, false, 1e-8 * std::sqrt(nE), 2000, &its, st);
+    s = adjoint_cg(h, Ld, Lp, gam, rhs2, s2, 1e-11 * std::sqrt(nE), 3000, sums + 12, st);
     if (s != KQR_OK) return done(s);
     masked_sums_kernel<<<grid_for(n), 256, 0, st>>>(s1, s2, mask, n, sums + 4);
     GK(cudaGetLastError());
