@@ -278,10 +278,10 @@ kqr_status kqr_profile_read(kqr_handle* h, int32_t kernel_id, int64_t* launches,
  * implicit differentiation through the KKT conditions of Sec. 4 at the
  * solution, holding the elbow set {i : tau - 1 < alpha_i < tau} fixed (the
  * loss is differentiable where no point enters or leaves it and no held-out
- * residual is zero).  The Gram products are recomputed in tiles (FP32 for the
- * adjoint terms, FP64-class for the held-out predictions); the adjoint solves
- * use the problem's preconditioner, whose core this call replaces.  Allocates
- * device memory; synchronises. */
+ * residual is zero).  The Gram products are recomputed in tiles, FP64-class
+ * throughout (the 1/lambda factors amplify product errors); the adjoint solves
+ * run CG on the problem's preconditioner, whose core this call replaces.
+ * Allocates device memory; synchronises. */
 kqr_status kqr_heldout_grad(kqr_handle* h, const double* X, const double* Xh, const double* yh, int64_t nh,
                             double* loss, double* d_loggamma, double* d_loglambda, double* dX);
 

@@ -19,7 +19,8 @@
 // multiplied element-wise by 1, the centred squared norm, or one coordinate:
 //   ((D o K) b)_i = |x_i|^2 (K b)_i + (K (|x|^2 o b))_i - 2 sum_c x_ic (K (x_c o b))_i,
 //   sum_j K_kj b_j (x_kc - x_jc) = x_kc (K b)_k - (K (x_c o b))_k,
-// so the Gram tiles are recomputed, never stored.
+// so the Gram tiles are recomputed, never stored.  Every product is FP64-class: the
+// 1/lambda factors and the cancellation in x_k (K b)_k - (K x b)_k amplify FP32 errors.
 #include <cmath>
 #include <vector>
 
@@ -98,21 +99,19 @@ __global__ void adjoint_kernel(const double* __restrict__ s1, const double* __re
 
 // Columns of a multi-RHS block: V[i * 8 + j] = base[i] * mult(col0 + j, i), where
 // multiplier index 0 is 1, index 1 is |x_i|^2, index 1 + c is x_ic (centred).
+// Columns of a multi-RHS block (row-major, ncols columns): V[i * ncols + j] =
+// base[i] * mult(col0 + j, i), where multiplier index 0 is 1 (or |x_i|^2 when
+// first_norm), and index 1 + c is x_ic (centred).
 __global__ void cols_kernel(const double* __restrict__ base, const double* __restrict__ xc, int64_t ldn,
                             const double* __restrict__ nrm, int64_t N, int col0, int ncols, int first_norm,
                             double* __restrict__ V) {
-  GRID_LOOP(e, N * 8) {
-    const int64_t i = e / 8;
-    const int j = (int)(e % 8);
-    double val = 0.0;
-    if (j < ncols) {
-      const int c = col0 + j;
-      double m = 1.0;
-      if (c == 0) m = first_norm ? nrm[i] : 1.0;
-      else m = xc[(size_t)(c - 1) * ldn + i];
-      val = base[i] * m;
-    }
-    V[e] = val;
+  GRID_LOOP(e, N * ncols) {
+    const int64_t i = e / ncols;
+    const int c = col0 + (int)(e % ncols);
+    double m = 1.0;
+    if (c == 0) m = first_norm ? nrm[i] : 1.0;
+    else m = xc[(size_t)(c - 1) * ldn + i];
+    V[e] = base[i] * m;
   }
 }
 
@@ -121,7 +120,7 @@ __global__ void scatter_cols_kernel(const double* __restrict__ U, int64_t N, int
   GRID_LOOP(e, N * ncols) {
     const int64_t i = e / ncols;
     const int j = (int)(e % ncols);
-    R[(size_t)(col0 + j) * ldr + i] = U[i * 8 + j];
+    R[(size_t)(col0 + j) * ldr + i] = U[e];
   }
 }
 
@@ -285,9 +284,7 @@ extern "C" kqr_status kqr_heldout_grad(kqr_handle* kh, const double* X, const do
   uo.rank0 = 2;
   uo.adaptive_rank = 0;
   uo.precond = KQR_PRECOND_NONE;
-  // CUDA-core FP32 products: the coordinate-weighted sums below cancel in x_k (K b)_k -
-  // (K x b)_k, where the three-TF32 tensor-core form (~2^-21 relative) loses a digit.
-  uo.rbf_tensor_cores = 0;
+  uo.rbf_tensor_cores = h->opt.rbf_tensor_cores;
   kqr_handle* ukh = nullptr;
   kqr_status s = kqr_create(Xu.data(), yu.data(), N, p, KQR_RBF, gamma, &uo, &ukh);
   if (s != KQR_OK) {
@@ -338,7 +335,7 @@ extern "C" kqr_status kqr_heldout_grad(kqr_handle* kh, const double* X, const do
   GK(gram_high(U, b1, Kb1, 1, st));
   heldout_kernel<<<grid_for(nh), 256, 0, st>>>(Kb1, yhd, n, nh, beta, tau, lam, b2, sums);
   GK(cudaGetLastError());
-  GK(gram_f32(U, b2, Kb2, 1, nullptr, st));
+  GK(gram_high(U, b2, Kb2, 1, st));
   // K_EE solves on the training problem: (K + gam 1 1^T + diag(L)) s = rhs with L tiny on E, huge off E.
   double* rhs1 = vec(h, V_B);
   double* rhs2 = vec(h, V_TMP);
@@ -347,7 +344,7 @@ extern "C" kqr_status kqr_heldout_grad(kqr_handle* kh, const double* X, const do
   double* s1 = vec(h, V_D);
   double* s2 = vec(h, V_DX);
   double* Lp = vec(h, V_LPRE);
-  elbow_kernel<<<grid_for(n), 256, 0, st>>>(h->st_v, Kb2, n, tau, lam, 1e-7, 1e12, 1e-10, rhs1, rhs2, Ld, mask, sums);
+  elbow_kernel<<<grid_for(n), 256, 0, st>>>(h->st_v, Kb2, n, tau, lam, 1e-7, 1e12, 0.0, rhs1, rhs2, Ld, mask, sums);
   GK(cudaGetLastError());
   GK(vec_copy(h, Lp, Ld, n, st));
   if (h->opt.precond == KQR_PRECOND_NYSTROM_DIAG) GK(axpy_vec(h, Lp, h->dres, 1.0, n, st));
@@ -387,9 +384,9 @@ extern "C" kqr_status kqr_heldout_grad(kqr_handle* kh, const double* X, const do
   for (int set = 0; set < 3; ++set) {
     for (int col0 = 0; col0 < ncol; col0 += 8) {
       const int nc = ncol - col0 < 8 ? ncol - col0 : 8;
-      cols_kernel<<<grid_for(N * 8), 256, 0, st>>>(bases[set], U->xc64, U->ldn, nrm, N, col0, nc, set == 0, V);
+      cols_kernel<<<grid_for(N * nc), 256, 0, st>>>(bases[set], U->xc64, U->ldn, nrm, N, col0, nc, set == 0, V);
       GK(cudaGetLastError());
-      GK(gram_f32(U, V, UU, 8, nullptr, st));
+      GK(gram_high(U, V, UU, nc, st));
       scatter_cols_kernel<<<grid_for(N * nc), 256, 0, st>>>(UU, N, col0, nc, ldr, outs[set]);
       GK(cudaGetLastError());
     }
