@@ -71,11 +71,14 @@ typedef enum kqr_kernel {
  *   tensor cores as three TF32 products (hi.hi + hi.lo + lo.hi of a TF32 split
  *   of X), unless options.rbf_tensor_cores = 0 (FP32 CUDA cores).
  * KQR_PREC_TF32: RBF only; one TF32 product on the tensor cores (about 2^-11
- *   relative error in the exponent's cross term). */
+ *   relative error in the exponent's cross term).
+ * KQR_PREC_BF16: RBF only; coordinates rounded to bf16 and one bf16 product on
+ *   the tensor cores (about 2^-8 relative error in the exponent's cross term). */
 typedef enum kqr_precision {
   KQR_PREC_HIGH = 0,
   KQR_PREC_FP32 = 1,
-  KQR_PREC_TF32 = 2
+  KQR_PREC_TF32 = 2,
+  KQR_PREC_BF16 = 3
 } kqr_precision;
 
 /* Preconditioner for the linear systems (2.1) and (3.1).

@@ -169,10 +169,24 @@ bool make_tmap_2d_f32_sw128(CUtensorMap* tm, void* base, int64_t inner, int64_t 
          CUDA_SUCCESS;
 }
 
+// Tensor map over a row-major [ldn][64] bf16 array, box 64 x 128 (128 bytes x 128 rows),
+// 128-byte swizzle: the K-major operand layout of tcgen05.mma kind::f16.
+bool make_tmap_rowmajor_bf16_sw128(CUtensorMap* tm, void* base, int64_t ldn) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {64, (cuuint64_t)ldn};
+  cuuint64_t strides[1] = {128};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 static void free_all(Handle* h) {
   void* bufs[] = {h->xs32, h->nrm32, h->hq, h->hl, h->exp_table, h->xc64, h->y, h->F32, h->dres, h->core, h->tvec,
                   h->Linv, h->part, h->v32, h->vec_pool, h->scal, h->red_counter, h->red_part, h->err_flag,
-                  h->st_alpha, h->st_v, h->st_z, h->sym_units, h->tc_hi, h->tc_lo};
+                  h->st_alpha, h->st_v, h->st_z, h->sym_units, h->tc_hi, h->tc_lo, h->tc_bf};
   for (void* b : bufs) dev_free(h, b);
   batch_free(h);
   if (h->scal_host) cudaFreeHost(h->scal_host);
@@ -479,6 +493,9 @@ kqr_status kqr_kmatvec_dev(kqr_handle* kh, const double* V, double* U, int64_t m
   else if (prec == KQR_PREC_TF32) {
     if (h->kind != KQR_RBF) return fail(h, KQR_INVALID_ARG, "KQR_PREC_TF32 applies to the RBF kernel only");
     e = gram_rbf_tc(h, V, U, (int)m, false, nullptr, st);
+  } else if (prec == KQR_PREC_BF16) {
+    if (h->kind != KQR_RBF) return fail(h, KQR_INVALID_ARG, "KQR_PREC_BF16 applies to the RBF kernel only");
+    e = gram_rbf_tc_bf16(h, V, U, (int)m, st);
   } else return fail(h, KQR_INVALID_ARG, "unknown precision");
   if (e != cudaSuccess) return cuda_fail(h, e, "Gram product");
   return KQR_OK;

@@ -21,6 +21,8 @@
 // stops issuing work and frees its tensor memory.
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "kqr_internal.h"
 #include "ptx.cuh"
 
@@ -46,6 +48,17 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint6
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// D[tmem] (+)= A[smem] B[smem]^T, bf16 inputs (both), FP32 accumulate.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -153,7 +166,9 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
     for (int u = 0; u < 4; ++u) racc[c][u] = 0.f;
   // kind::tf32, FP32 accumulate, A and B K-major, N = 128, M = 128
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  // FP32 accumulate, A and B K-major, N = 128, M = 128; operands TF32 (kind::tf32) or bf16 (kind::f16)
+  const uint32_t idesc = (1u << 4) | (NTERMS == 0 ? (1u << 7) | (1u << 10) : (2u << 7) | (2u << 10)) |
+                         ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
   for (int q = 0; q <= nt; ++q) {
     if (q < nt && tid < 128) {
@@ -173,7 +188,8 @@ __global__ void __launch_bounds__(256, 1)
         const unsigned char* bl = XJl[q & 1];
         for (int k = 0; k < ksteps; ++k) {
           const uint32_t off = (uint32_t)(k >> 2) * kAtomBytes + (uint32_t)(k & 3) * 32u;
-          umma_tf32(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bh + off), idesc, k > 0 ? 1u : 0u);
+          if (NTERMS == 0) umma_bf16(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bh + off), idesc, k > 0 ? 1u : 0u);
+          else umma_tf32(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bh + off), idesc, k > 0 ? 1u : 0u);
           if (NTERMS == 3) {
             umma_tf32(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bl + off), idesc, 1u);
             umma_tf32(d, umma_desc_sw128(XIl + off), umma_desc_sw128(bh + off), idesc, 1u);
@@ -343,14 +359,15 @@ cudaError_t rbf_tc_prepare(Handle* h) {
 
 template <int M, int NT>
 static cudaError_t launch_tc(Handle* h, int splits, int tps, int ksteps, cudaStream_t st) {
-  const int katoms = h->tc_Kp / 32;
+  const int katoms = NT == 0 ? 1 : h->tc_Kp / 32;
   const size_t smem = tc_smem(katoms, M);
   auto kern = gram_rbf_tc_kernel<M, NT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int row_tiles = (int)(h->ldn / kTile);
   prof_mark(h, 0, true, st);
-  kern<<<dim3(row_tiles, splits), 256, smem, st>>>(h->tm_tc_hi, h->tm_tc_lo, h->nrm32, h->v32, h->part, ksteps,
+  kern<<<dim3(row_tiles, splits), 256, smem, st>>>(NT == 0 ? h->tm_tc_bf : h->tm_tc_hi, h->tm_tc_lo, h->nrm32,
+                                                   h->v32, h->part, ksteps,
                                                    katoms, (int)h->ldn, tps, row_tiles, h->tc_fold_rows,
                                                    h->err_flag);
   prof_mark(h, 0, false, st);
@@ -358,14 +375,40 @@ static cudaError_t launch_tc(Handle* h, int splits, int tps, int ksteps, cudaStr
   return cudaGetLastError();
 }
 
-// U = K V on the tensor cores; three_terms selects FP32 (hi.hi + hi.lo + lo.hi) or TF32 (hi.hi).
-cudaError_t gram_rbf_tc(Handle* h, const double* V, double* U, int m, bool three_terms, const GramEpilogue* ep,
-                        cudaStream_t st) {
+// row-major bf16 copy [ldn][64] of xs32 (feature-major), round to nearest, zero padded.
+__global__ void bf16_copy_kernel(const float* __restrict__ xs32, int64_t ldn, int p,
+                                 __nv_bfloat16* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ldn * 64; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / 64;
+    const int k = (int)(e % 64);
+    out[e] = __float2bfloat16_rn(k < p ? xs32[(size_t)k * ldn + i] : 0.f);
+  }
+}
+
+bool make_tmap_rowmajor_bf16_sw128(CUtensorMap* tm, void* base, int64_t ldn);
+
+static cudaError_t rbf_bf16_prepare(Handle* h) {
+  if (h->tc_bf) return cudaSuccess;
+  h->tc_bf = (__nv_bfloat16*)dev_alloc(h, (size_t)h->ldn * 64 * sizeof(__nv_bfloat16));
+  if (!h->tc_bf) return cudaErrorMemoryAllocation;
+  bf16_copy_kernel<<<grid_for(h->ldn * 64), 256, 0, h->stream>>>(h->xs32, h->ldn, (int)h->p, h->tc_bf);
+  h->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (!make_tmap_rowmajor_bf16_sw128(&h->tm_tc_bf, h->tc_bf, h->ldn)) return cudaErrorInvalidValue;
+  return cudaStreamSynchronize(h->stream);
+}
+
+// U = K V on the tensor cores; nt = 3: FP32 class (TF32 hi.hi + hi.lo + lo.hi), 1: TF32 (hi.hi),
+// 0: bf16 (one term, K = 16 per instruction).
+static cudaError_t rbf_tc_product(Handle* h, const double* V, double* U, int m, int nt, const GramEpilogue* ep,
+                                  cudaStream_t st) {
   cudaError_t e = rbf_tc_prepare(h);
   if (e != cudaSuccess) return e;
+  if (nt == 0 && (e = rbf_bf16_prepare(h)) != cudaSuccess) return e;
   const int M = m <= 1 ? 1 : (m <= 2 ? 2 : (m <= 4 ? 4 : 8));
   const int row_tiles = (int)(h->ldn / kTile), col_tiles = row_tiles;
-  const int katoms = h->tc_Kp / 32;
+  const int katoms = nt == 0 ? 1 : h->tc_Kp / 32;
   const int resident = tc_smem(katoms, M) * 2 <= 228 * 1024 ? 2 : 1;
   const int target = 8 * resident * h->num_sms;
   int s = (target + row_tiles - 1) / row_tiles;
@@ -394,8 +437,15 @@ cudaError_t gram_rbf_tc(Handle* h, const double* V, double* U, int m, bool three
   tc_to_f32_kernel<<<grid_for(h->ldn * M), 256, 0, st>>>(V, h->v32, h->n, h->ldn, m, M, sum_out);
   h->launches++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int ksteps = (int)((h->p + 7) / 8);
-  if (three_terms) {
+  const int ksteps = nt == 0 ? (int)((h->p + 15) / 16) : (int)((h->p + 7) / 8);
+  if (nt == 0) {
+    switch (M) {
+      case 1: e = launch_tc<1, 0>(h, splits, tps, ksteps, st); break;
+      case 2: e = launch_tc<2, 0>(h, splits, tps, ksteps, st); break;
+      case 4: e = launch_tc<4, 0>(h, splits, tps, ksteps, st); break;
+      default: e = launch_tc<8, 0>(h, splits, tps, ksteps, st); break;
+    }
+  } else if (nt == 3) {
     switch (M) {
       case 1: e = launch_tc<1, 3>(h, splits, tps, ksteps, st); break;
       case 2: e = launch_tc<2, 3>(h, splits, tps, ksteps, st); break;
@@ -415,6 +465,15 @@ cudaError_t gram_rbf_tc(Handle* h, const double* V, double* U, int m, bool three
   tc_reduce_kernel<<<grid_for(h->n * m), 256, 0, st>>>(h->part, splits, h->ldn, M, m, h->n, U, g);
   h->launches++;
   return cudaGetLastError();
+}
+
+cudaError_t gram_rbf_tc(Handle* h, const double* V, double* U, int m, bool three_terms, const GramEpilogue* ep,
+                        cudaStream_t st) {
+  return rbf_tc_product(h, V, U, m, three_terms ? 3 : 1, ep, st);
+}
+
+cudaError_t gram_rbf_tc_bf16(Handle* h, const double* V, double* U, int m, cudaStream_t st) {
+  return rbf_tc_product(h, V, U, m, 0, nullptr, st);
 }
 
 }  // namespace kqr

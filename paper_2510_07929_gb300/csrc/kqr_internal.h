@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,6 +57,8 @@ cudaError_t gram_f32(Handle* h, const double* V, double* U, int m, const GramEpi
 // (three TF32 terms) or TF32 (one term); ep as for gram_f32.
 cudaError_t gram_rbf_tc(Handle* h, const double* V, double* U, int m, bool three_terms, const GramEpilogue* ep,
                         cudaStream_t st);
+// RBF product with the cross term as one bf16 tensor-core product (KQR_PREC_BF16).
+cudaError_t gram_rbf_tc_bf16(Handle* h, const double* V, double* U, int m, cudaStream_t st);
 // m = 1 product with each off-diagonal tile formed once (gram_f32_sym.cu).
 cudaError_t gram_f32_sym(Handle* h, const double* V, double* U, const GramEpilogue* ep, cudaStream_t st);
 cudaError_t gram_high(Handle* h, const double* V, double* U, int m, cudaStream_t st);
@@ -112,6 +115,8 @@ struct Handle {
   int tc_Kp = 0;
   int tc_fold_rows = 0;   // apply exp2(-|xs_i|^2) to finished row sums (all norms < 60)
   CUtensorMap tm_tc_hi{}, tm_tc_lo{};
+  __nv_bfloat16* tc_bf = nullptr;     // row-major bf16 copy [ldn][64] (KQR_PREC_BF16)
+  CUtensorMap tm_tc_bf{};
 
   // Symmetric Gram product: work-unit table (row tile, first and end column tile).
   int4* sym_units = nullptr;

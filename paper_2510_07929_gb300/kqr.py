@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libkqr.so")
 
 RBF, LAPLACIAN = 0, 1
-PREC_HIGH, PREC_FP32, PREC_TF32 = 0, 1, 2
+PREC_HIGH, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 3
 PRECOND_NYSTROM_DIAG, PRECOND_PAPER, PRECOND_NONE = 0, 1, 2
 KIND = {"rbf": RBF, "laplacian": LAPLACIAN}
 

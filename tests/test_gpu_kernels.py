@@ -86,6 +86,33 @@ def test_tf32_gram_error_is_bounded(K_, n, p):
     assert err_fp32 < err_tf32
 
 
+@pytest.mark.parametrize("n,p", [(3001, 20), (515, 50), (257, 3)])
+def test_bf16_gram_error_is_bounded(K_, n, p):
+    """KQR_PREC_BF16 (coordinates rounded to bf16, 2^-9 each, one bf16 product
+    for the cross term): the cross term errs by at most 2^-8 |xs_i||xs_j|, so
+    entries err by about 2^-7 |xs|^2 ln 2 relative; check that bound (2x margin)
+    and that TF32 is more accurate."""
+    wl = _data("rbf", n, p)
+    v = W.random_vectors(n, seed=4)
+    ref = O.kmatvec(wl.X, v, "rbf", wl.gamma)
+    absref = O.kmatvec(wl.X, np.abs(v), "rbf", wl.gamma)
+    Xc = wl.X - wl.X.mean(0)
+    s2 = wl.gamma / np.log(2.0) * np.max(np.sum(Xc * Xc, axis=1))   # max |xs|^2
+    with K_.Problem(wl.X, wl.y, "rbf", wl.gamma) as prob:
+        u_bf16 = prob.kmatvec(v, K_.PREC_BF16)
+        u_tf32 = prob.kmatvec(v, K_.PREC_TF32)
+        V3 = W.random_vectors(n, 3, seed=5)
+        u3 = prob.kmatvec(V3, K_.PREC_BF16)
+    err_bf16 = np.max(np.abs(u_bf16 - ref) / absref)
+    err_tf32 = np.max(np.abs(u_tf32 - ref) / absref)
+    bound = 2.0 ** -6 * s2 * np.log(2.0) + 1e-5
+    assert err_bf16 <= bound, (err_bf16, bound)
+    assert err_tf32 < err_bf16
+    ref3 = O.kmatvec(wl.X, V3, "rbf", wl.gamma)
+    abs3 = O.kmatvec(wl.X, np.abs(V3), "rbf", wl.gamma)
+    assert np.max(np.abs(u3 - ref3) / abs3) <= bound
+
+
 def test_gram_device_entry_and_stream(K_):
     import torch
 
