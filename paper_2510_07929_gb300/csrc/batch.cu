@@ -102,8 +102,23 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
       : "memory");
 }
 
-// 32 consecutive 32-bit columns of this thread's TMEM lane, then wait for the stores.
-__device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t* v) {
+// Issue a load of 32 consecutive 32-bit columns of this thread's TMEM lane (no wait).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Issue a store of 32 consecutive 32-bit columns of this thread's TMEM lane (no wait).
+__device__ __forceinline__ void tmem_st32_nowait(uint32_t taddr, const uint32_t* v) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
       "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
@@ -113,7 +128,6 @@ __device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t* v) 
       "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
       "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
       : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
@@ -383,22 +397,26 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
         fence_after();
         // the step's column norms arrived with V_J (the stage stays until this step's second MMA)
         const float4* nj4 = reinterpret_cast<const float4*>(base + kOffV + vs * kVStride + kVBytes);
-#pragma unroll 1
+        // both 32-column halves of the S row in flight at once, one wait
+        uint32_t graw[64];
+        tmem_ld32_nowait(tmem + (uint32_t)(sb * 64) + lane_off, graw);
+        tmem_ld32_nowait(tmem + (uint32_t)(sb * 64 + 32) + lane_off, graw + 32);
+        tmem_wait_ld();
+#pragma unroll
         for (int ch = 0; ch < 2; ++ch) {
-          float g[32];
-          tmem_load32(tmem + (uint32_t)(sb * 64 + ch * 32) + lane_off, g);
           uint32_t e[32];
 #pragma unroll
           for (int c4 = 0; c4 < 8; ++c4) {
             const float4 nn = nj4[ch * 8 + c4];
-            e[4 * c4 + 0] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 0], -(ni + nn.x))));
-            e[4 * c4 + 1] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 1], -(ni + nn.y))));
-            e[4 * c4 + 2] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 2], -(ni + nn.z))));
-            e[4 * c4 + 3] = tf32_rna(ex2_approx(fmaf(2.f, g[4 * c4 + 3], -(ni + nn.w))));
+            const uint32_t* g = graw + ch * 32 + 4 * c4;
+            e[4 * c4 + 0] = tf32_rna(ex2_approx(fmaf(2.f, __uint_as_float(g[0]), -(ni + nn.x))));
+            e[4 * c4 + 1] = tf32_rna(ex2_approx(fmaf(2.f, __uint_as_float(g[1]), -(ni + nn.y))));
+            e[4 * c4 + 2] = tf32_rna(ex2_approx(fmaf(2.f, __uint_as_float(g[2]), -(ni + nn.z))));
+            e[4 * c4 + 3] = tf32_rna(ex2_approx(fmaf(2.f, __uint_as_float(g[3]), -(ni + nn.w))));
           }
           if (PT) {
             // P tile in tensor memory, lane = row, columns [32 ch, 32 ch + 32)
-            tmem_store32(tmem + kPCol + (uint32_t)(pb * 64 + ch * 32) + lane_off, e);
+            tmem_st32_nowait(tmem + kPCol + (uint32_t)(pb * 64 + ch * 32) + lane_off, e);
           } else {
             // columns [32 ch, 32 ch + 32) are swizzle atom ch of the P tile in shared memory
             unsigned char* prow = base + kOffP + pb * kPBytes + ch * kPAtom + r * 128;
@@ -408,6 +426,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
                   make_uint4(e[4 * c], e[4 * c + 1], e[4 * c + 2], e[4 * c + 3]);
           }
         }
+        if (PT) tmem_wait_st();
         fence_before();
         if (!PT) fence_async_smem();
         __syncwarp();
