@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--path-tau", type=float, default=0.5)
     ap.add_argument("--path-lambdas", type=int, default=50)
     ap.add_argument("--path-precond", type=int, default=0, help="0 Nystrom+diag, 1 paper, 2 none (NALM)")
+    ap.add_argument("--path-first", type=int, nargs=2, default=None, metavar=("START", "STOP"),
+                    help="--mode path: solve only lambdas[START:STOP] of the grid")
+    ap.add_argument("--path-cg-high", type=int, default=2,
+                    help="--mode path: CG products 0 FP32, 1 FP64-class, 2 FP64-class when K is numerically low-rank")
     ap.add_argument("--prec-taus", default="0.5", help="comma-separated tau values for --mode precision")
     ap.add_argument("--batch-p-in-smem", action="store_true",
                     help="--mode batch: stage the Gram tile through shared memory instead of tensor memory")
@@ -462,8 +466,11 @@ def run_path(args):
     tol = 1e-8
     wl = W.yuan2006(n=n, gamma=args.path_gamma, tau=args.path_tau)
     lams = np.logspace(-2, 0, args.path_lambdas)
+    if args.path_first:
+        lams = lams[args.path_first[0]:args.path_first[1]]
     t0 = time.perf_counter()
-    prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, precond=args.path_precond, time_limit_s=args.time_limit)
+    prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, precond=args.path_precond, time_limit_s=args.time_limit,
+                       cg_high=args.path_cg_high)
     t_setup = time.perf_counter() - t0
     per, worst, unsolved, products = [], 0.0, 0, 0
     for lam in lams:
@@ -482,6 +489,7 @@ def run_path(args):
     key = (n, args.path_gamma, args.path_tau)
     out = {"mode": "path", "workload": f"yuan2006 n={n} p=2 rbf gamma={args.path_gamma:g} tau={args.path_tau:g}",
            "lambdas": len(lams), "tol": tol, "precond": ["nystrom_diag", "paper", "none"][args.path_precond],
+           "cg_products": ["fp32", "fp64-class", "auto"][args.path_cg_high],
            "total_s": total, "setup_s": t_setup, "median_solve_s": float(np.median(per)), "max_solve_s": max(per),
            "worst_kkt_or_gap": worst, "not_converged": unsolved, "gram_products": products,
            "paper_total_s": PAPER_TABLE1_S.get(key), "paper_hardware": "MATLAB, Xeon Platinum 8375C, 128 cores"}

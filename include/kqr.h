@@ -133,6 +133,9 @@ typedef struct kqr_options {
   int32_t cg_tf32;               /* RBF only, 1: CG products in TF32 on tcgen05 (one term), each linear solve
                                     iteratively refined against FP32 residuals to the same tolerance */
   int32_t verbose;               /* 1: one line per outer iteration on stderr */
+  int32_t cg_high;               /* CG products: 0 FP32; 1 FP64-class; 2 FP64-class when K is numerically
+                                    low-rank at FP32 resolution (RPCholesky's mean residual diagonal below
+                                    2^-24 n), where FP32 products cannot resolve most of the spectrum */
 } kqr_options;
 
 /* Counters and final residuals of a solve (Sec. 4 definitions). */

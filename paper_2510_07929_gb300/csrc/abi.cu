@@ -372,6 +372,7 @@ void kqr_default_options(kqr_options* o) {
   o->symmetric_gram = 1;
   o->rbf_tensor_cores = 1;
   o->verbose = 0;
+  o->cg_high = 0;
 }
 
 void kqr_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*), void* ctx) {
@@ -583,6 +584,7 @@ kqr_status kqr_pcg_dev(kqr_handle* kh, const double* Ldiag, double gam, const do
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
   KQR_SINGLE(h);
+  h->cg_high_on = false;   // the parity entry point always runs FP32 products
   if (!Ldiag || !b || !x) return fail(h, KQR_INVALID_ARG, "null vector");
   if (!(gam >= 0) || !(tol > 0) || maxit < 1) return fail(h, KQR_INVALID_ARG, "bad gam/tol/maxit");
   cudaStream_t st = pick_stream(h, stream);

@@ -150,6 +150,8 @@ struct Handle {
   size_t prof_used[2] = {0, 0};
   int num_sms = 0;
   int64_t cg_truncations = 0;         // CG runs stopped at a non-positive curvature
+  double dres_mean = 1.0;             // RPCholesky's mean residual diagonal (before the floor)
+  bool cg_high_on = false;            // this solve's CG products are FP64-class
   BatchData* batch = nullptr;         // set for batched-product handles (batch.cu)
 };
 

@@ -744,6 +744,7 @@ kqr_status rpcholesky_setup(Handle* h, const double* uniforms) {
   }
   double tot = 0.0;
   for (double v : hsum) tot += v;
+  h->dres_mean = tot / (double)n;
   floor_kernel<<<grid_for(n), 256, 0, st>>>(h->dres, n, 0.1 * tot / (double)n);
   h->launches++;
   e = cudaStreamSynchronize(st);

@@ -51,6 +51,30 @@ static kqr_status check_device_flag(Handle* h, cudaStream_t st) {
   return KQR_OK;
 }
 
+// Ap = K p + gam (1^T p) 1 + L o p with the FP64-class product; Kp = K p; pAp into *dot.
+__global__ void high_op_kernel(double* __restrict__ Ap, const double* __restrict__ Kp, const double* __restrict__ p,
+                               const double* __restrict__ L, const double* __restrict__ sump, double gam, int64_t n) {
+  const double sg = gam * (*sump);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Ap[i] = Kp[i] + sg + L[i] * p[i];
+}
+
+static cudaError_t high_operator(Handle* h, const double* p, double* Ap, double* Kp, const double* L, double gam,
+                                 double* sump, double* dot, cudaStream_t st) {
+  RedArgs rs;
+  rs.a = p;
+  cudaError_t e = reduce(h, RED_SUM, rs, h->n, sump, st);
+  if (e != cudaSuccess) return e;
+  if ((e = gram_high(h, p, Kp, 1, st)) != cudaSuccess) return e;
+  high_op_kernel<<<grid_for(h->n), 256, 0, st>>>(Ap, Kp, p, L, sump, gam, h->n);
+  h->launches++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  RedArgs rd;
+  rd.a = p;
+  rd.b = Ap;
+  return reduce(h, RED_DOT, rd, h->n, dot, st);
+}
+
 kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const double* b, double* x, double* Kx,
                bool warm, double tol, int maxit, int* iters, cudaStream_t st, bool lowprec) {
   const int64_t n = h->n;
@@ -92,7 +116,8 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
     ep.pvec = p;
     ep.dot_out = h->scal + S_PAP;
     ep.raw_out = Kp;
-    if (lowprec) CK(gram_rbf_tc(h, p, Ap, 1, false, &ep, st));
+    if (h->cg_high_on && !lowprec) CK(high_operator(h, p, Ap, Kp, L, gam, h->scal + S_SUMP, h->scal + S_PAP, st));
+    else if (lowprec) CK(gram_rbf_tc(h, p, Ap, 1, false, &ep, st));
     else CK(gram_f32(h, p, Ap, 1, &ep, st));
     CK(fetch(h, S_PAP, 1, st));
     const double pAp = h->scal_host[S_PAP];
@@ -247,6 +272,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
   double* S = vec(h, V_S);
   const double* dres = (o.precond == KQR_PRECOND_NYSTROM_DIAG) ? h->dres : nullptr;
   const bool mixed = o.cg_tf32 && h->kind == KQR_RBF;
+  h->cg_high_on = !mixed && (o.cg_high == 1 || (o.cg_high == 2 && h->dres_mean < std::ldexp((double)n, -24)));
   kqr_info inf{};
   inf.rank = h->r;
   const int64_t builds0 = h->core_builds;
@@ -286,7 +312,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
                      &inf.matvecs_low, st));
     } else {
       KS(pcg(h, L, Lpre, lam * sigma, b, alpha, Ka, k > 0, eps_k, o.pcg_maxit, &its, st));
-      inf.matvecs_fp32 += its;
+      (h->cg_high_on ? inf.matvecs_high : inf.matvecs_fp32) += its;
     }
     inf.pcg_iters += its;
     RedArgs rs;
@@ -358,7 +384,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
                          &inf.matvecs_low, st));
         } else {
           KS(pcg(h, L, Lpre, lam * sigma, b, d, Kd, false, ptol, o.pcg_maxit, &its, st));
-          inf.matvecs_fp32 += its;
+          (h->cg_high_on ? inf.matvecs_high : inf.matvecs_fp32) += its;
         }
         inf.pcg_iters += its;
         // Armijo backtracking on phi_k(alpha + c d) - phi_k(alpha), term by term.

@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
         ("core_reuse_rtol", ctypes.c_double),
         ("time_limit_s", ctypes.c_double), ("phase1_only", ctypes.c_int32),
         ("symmetric_gram", ctypes.c_int32), ("rbf_tensor_cores", ctypes.c_int32), ("cg_tf32", ctypes.c_int32),
-        ("verbose", ctypes.c_int32),
+        ("verbose", ctypes.c_int32), ("cg_high", ctypes.c_int32),
     ]
 
 

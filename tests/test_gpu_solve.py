@@ -90,6 +90,16 @@ def test_low_rank_rbf_solve_survives_rounding_curvature(K_, lam):
     check_against_oracle(wl, alpha, beta, v, z, kkt)
 
 
+@pytest.mark.parametrize("cg_high", [1, 2])
+def test_fp64_class_cg_products_match_oracle(K_, cg_high):
+    """CG with FP64-class products (always, or automatically because this p = 2
+    RBF kernel is numerically low-rank at FP32 resolution): same contract."""
+    wl = W.yuan2006(n=1500, gamma=0.1, tau=0.5, lam=1e-2)
+    alpha, beta, v, z, kkt, info = gpu_solve(K_, wl, tol=1e-7, cg_high=cg_high)
+    assert info["status"] == K_.OK and info["matvecs_fp32"] == 0 and info["matvecs_high"] > info["pcg_iters"] // 2
+    check_against_oracle(wl, alpha, beta, v, z, kkt)
+
+
 @pytest.mark.parametrize("precond", [1, 2])
 def test_paper_preconditioner_and_plain_cg_converge(K_, precond):
     wl = W.rbf_small(n=900, seed=5)
