@@ -512,28 +512,9 @@ __global__ void gather_col_kernel(const double* __restrict__ V, double* __restri
     out[i] = V[i * m + c];
 }
 
-__global__ void column_kernel(const double* __restrict__ xc, int64_t n, int64_t ldn, int p, int64_t s, double gamma,
-                              int lap, double* __restrict__ col) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double d = 0.0;
-    for (int k = 0; k < p; ++k) {
-      const double t = xc[(size_t)k * ldn + i] - xc[(size_t)k * ldn + s];
-      d = lap ? d + fabs(t) : fma(t, t, d);
-    }
-    col[i] = exp(-gamma * d);
-  }
-}
-
 static size_t lap_high_smem(int p) {
   return (size_t)6 * p * kTile * 4 + (size_t)(1 << kTB) * sizeof(float2) + 2 * kTile * sizeof(double) +
          4 * sizeof(uint64_t);
-}
-
-cudaError_t gram_column(Handle* h, int64_t s, double* col, cudaStream_t st) {
-  column_kernel<<<grid_for(h->n), 256, 0, st>>>(h->xc64, h->n, h->ldn, (int)h->p, s, h->gamma,
-                                                h->kind == KQR_LAPLACIAN, col);
-  h->launches++;
-  return cudaGetLastError();
 }
 
 cudaError_t gram_high(Handle* h, const double* V, double* U, int m, cudaStream_t st) {

@@ -65,7 +65,6 @@ cudaError_t gram_high(Handle* h, const double* V, double* U, int m, cudaStream_t
 // Laplacian m = 1 FP64-class product with each off-diagonal tile formed once (gram_high_sym.cu).
 cudaError_t gram_high_sym(Handle* h, const double* V, double* U, cudaStream_t st);
 // Column s of K in FP64 (RPCholesky).
-cudaError_t gram_column(Handle* h, int64_t s, double* col, cudaStream_t st);
 
 struct Handle {
   int device = 0;
