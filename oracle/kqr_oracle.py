@@ -23,6 +23,7 @@ import dataclasses
 import math
 
 import numpy as np
+import scipy.linalg as _sla
 
 RBF = "rbf"
 LAPLACIAN = "laplacian"
@@ -282,8 +283,8 @@ class Options:
 def _admm_sigma_update(sigma: float, k: int, res: dict, o: Options) -> float:
     """Residual balancing between eta_p (stationarity) and eta_d (consensus
     feasibility), every ``balance_every`` iterations (reading of Alg. 1's
-    free sigma)."""
-    if (k + 1) % o.balance_every != 0:
+    free sigma); ``balance_every <= 0`` keeps sigma fixed."""
+    if o.balance_every <= 0 or (k + 1) % o.balance_every != 0:
         return sigma
     if res["eta_d"] > o.balance_ratio * res["eta_p"]:
         return sigma * o.balance_factor
@@ -294,8 +295,9 @@ def _admm_sigma_update(sigma: float, k: int, res: dict, o: Options) -> float:
 
 def admm(K, y, tau: float, lam: float, o: Options, beta: float = 0.0, z=None, v=None):
     """Phase I, Algorithm 1 (inexact ADMM on (1.4)); the alpha-system
-    M alpha = b_k is solved exactly here (Cholesky), which satisfies every
-    inexactness bound eps_k >= 0.  Starts from beta = 0, z = v = 0 unless given.
+    M alpha = b_k is solved exactly here (Cholesky factor of the SPD M, reused
+    while sigma is unchanged), which satisfies every inexactness bound
+    eps_k >= 0.  Starts from beta = 0, z = v = 0 unless given.
     Stops when max(eta_kkt, eta_gap) <= admm_tol or after admm_maxit (Sec. 4)."""
     n = y.size
     z = np.zeros(n) if z is None else np.array(z, dtype=np.float64)
@@ -309,9 +311,9 @@ def admm(K, y, tau: float, lam: float, o: Options, beta: float = 0.0, z=None, v=
     for k in range(o.admm_maxit):
         if chol is None:
             M = K + lam * sigma * (np.eye(n) + np.outer(ones, ones))
-            chol = np.linalg.cholesky(M)
+            chol = _sla.cho_factor(M, lower=True)
         b = lam * (y - beta * ones - z + sigma * v)
-        alpha = np.linalg.solve(chol.T, np.linalg.solve(chol, b))
+        alpha = _sla.cho_solve(chol, b)
         v = proj_box(alpha + z / sigma, tau)
         beta = beta + o.gamma_admm * sigma * alpha.sum()
         z = z + o.gamma_admm * sigma * (alpha - v)
@@ -327,8 +329,9 @@ def admm(K, y, tau: float, lam: float, o: Options, beta: float = 0.0, z=None, v=
 def ssn(K, y, tau: float, lam: float, beta: float, z, sigma: float, alpha0, o: Options, tol_grad: float):
     """Algorithm 3 (semismooth Newton on phi_k) with Armijo backtracking.  The
     regularised Newton system (H_t + eps_t I) d = -grad is solved exactly
-    (Cholesky), which meets the PCG accuracy bound of Alg. 3.  Stops when
-    ||grad phi_k|| <= tol_grad or after ssn_maxit steps.  The Armijo test
+    (Cholesky: every generalized Hessian is positive definite), which meets
+    the PCG accuracy bound of Alg. 3.  Stops when ||grad phi_k|| <= tol_grad
+    or after ssn_maxit steps.  The Armijo test
     phi(alpha + c d) <= phi(alpha) + mu c <grad, d> is evaluated on the
     difference phi(alpha + c d) - phi(alpha), term by term."""
     n = y.size
@@ -345,7 +348,7 @@ def ssn(K, y, tau: float, lam: float, beta: float, z, sigma: float, alpha0, o: O
         eps = o.tau1 * min(o.tau2, ng)
         S = jacobian_diag(w, tau)
         H = K / lam + sigma * (np.outer(ones, ones) + np.diag(1.0 - S)) + eps * np.eye(n)
-        d = np.linalg.solve(H, -g)
+        d = _sla.cho_solve(_sla.cho_factor(H, lower=True), -g)
         Kd = K @ d
         gd = float(g @ d)
         s0 = alpha.sum() + beta / sigma
@@ -467,14 +470,21 @@ def certified_gap(alpha, K, y, tau: float, lam: float, theta=None) -> dict:
     (theta - a)^T K (theta - a) >= 0), so the gap bounds how far both are from
     the optimum.  Leaving theta unprojected keeps the 1/lambda factor of the
     primal residual away from the projection step."""
-    y = np.asarray(y, dtype=np.float64)
     theta = np.asarray(alpha if theta is None else theta, dtype=np.float64)
     a = project_feasible(alpha, tau)
-    Kt = K @ theta
-    Ka = K @ a
-    r = y - Kt / lam
+    return certified_gap_from_products(theta, a, K @ theta, K @ a, y, tau, lam)
+
+
+def certified_gap_from_products(theta, a, Ktheta, Ka, y, tau: float, lam: float) -> dict:
+    """The weak-duality certificate of ``certified_gap`` from the products
+    K theta and K a (for sizes where K cannot be formed); ``a`` must be the
+    feasible projection of alpha (``project_feasible``)."""
+    y = np.asarray(y, dtype=np.float64)
+    theta = np.asarray(theta, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    r = y - np.asarray(Ktheta) / lam
     beta = quantile_intercept(r, tau)
-    P = check_loss(r - beta, tau) + float(theta @ Kt) / (2.0 * lam)
+    P = check_loss(r - beta, tau) + float(theta @ Ktheta) / (2.0 * lam)
     D = -float(a @ Ka) / (2.0 * lam) + float(y @ a)
     return dict(gap=(P - D) / (1.0 + abs(P) + abs(D)), P=P, D=D, beta=beta, alpha=a)
 

@@ -331,3 +331,38 @@ def test_kkt_residuals_vanish_at_closed_form_solution():
     assert res["eta_kkt"] < 1e-15 and res["eta_gap"] < 1e-15
     bad = O.kkt_residuals(a, a.copy(), beta + 0.1, z, y, K @ a, c["tau"], c["lam"])
     assert bad["eta_p"] == pytest.approx(0.1 * math.sqrt(2) / (1 + np.linalg.norm(y)))
+
+
+def test_kkt_residuals_three_point_golden():
+    """Sec. 4 residuals at a hand-computed point with z != 0, alpha != v and
+    1^T alpha != 0 (tests/golden/kkt_three_point.json): pins eta_d and eta_c,
+    which vanish at any solution and so are not fixed by the closed forms."""
+    c = json.load(open(os.path.join(GOLDEN, "kkt_three_point.json")))
+    env = {"sqrt": math.sqrt, "log": math.log}
+    X = np.array(c["x"])
+    K = O.gram(X, X, c["kind"], eval(c["gamma"], env))
+    np.testing.assert_allclose(K, [[eval(s, env) for s in row] for row in c["K"]], rtol=1e-15)
+    a, v, z, y = (np.array(c[k]) for k in ("alpha", "v", "z", "y"))
+    res = O.kkt_residuals(a, v, c["beta"], z, y, K @ a, c["tau"], c["lam"])
+    for key, expr in c["expected"].items():
+        assert res[key] == pytest.approx(eval(expr, env), rel=1e-13), key
+    assert res["eta_kkt"] == max(res["eta_p"], res["eta_d"], res["eta_c"])
+
+
+@pytest.mark.parametrize("kind", [O.RBF, O.LAPLACIAN])
+def test_native_products_match_numpy_oracle(kind):
+    """The oracle's C form of K and K.V (kernel_native.c, used at sizes numpy
+    cannot reach) against the numpy definitions, on ragged sizes and row subsets."""
+    from oracle import native as N
+
+    rng = np.random.default_rng(31)
+    X = rng.standard_normal((1037, 7))
+    Z = rng.standard_normal((515, 7))
+    V = rng.standard_normal((1037, 3))
+    ref = O.kmatvec(X, V, kind, 0.3)
+    np.testing.assert_allclose(N.kmatvec(X, V, kind, 0.3), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    rows = rng.choice(1037, 33, replace=False)
+    np.testing.assert_allclose(N.kmatvec(X, V[:, 1], kind, 0.3, rows=rows), ref[rows, 1], rtol=1e-12,
+                               atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_allclose(N.gram(X[:40], Z, kind, 0.3), O.gram(X[:40], Z, kind, 0.3), rtol=1e-13, atol=1e-300)
+    assert N.threads() >= 1
