@@ -27,16 +27,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "KQR solve sec to KKT≤1e-6 at n=200k; fused K·V TFLOP/s and % of roofline"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128          # FP32 FFMA/FADD lanes per SM (measured unit rate, see the design notes)
+SM_COUNT_FALLBACK = 152          # used only when the device cannot be queried
+SM_MAX_MHZ_FALLBACK = 2070.0     # used only when nvidia-smi gives no maximum clock
 # DRAM bytes (read + write) per launch of gram_f32_sym_kernel on the n = 200000, p = 50
 # Laplacian workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum).
 SYM_LAPLACIAN_TRAFFIC = {(200000, 50): 42469632 + 8192}
-# Gram products (FP32 + FP64-class) of one solve of the default workload with
-# the library's default constants; the reference arm, which cannot run the
-# solver, scales the oracle's per-product time by it.
-REF_PRODUCTS_PER_SOLVE = 330
+# Rows of the workload the oracle's full reference solve uses (dense FP64, Alg. 1
+# then Alg. 2/3): the full n = 200000 problem is far beyond it in a bench run.
+REF_SUBSAMPLE_ROWS = 2000
+# Seconds of multi-core oracle K.v work that the CPU baseline's projection samples.
+CPU_SAMPLE_SECONDS = 15.0
 
 
 def parse():
@@ -139,18 +140,49 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_matvec_seconds(wl, rows: int = 96, seed: int = 0):
-    """Seconds for one full FP64 oracle K.v on this workload, from a timed
-    sample of ``rows`` rows scaled by n / rows."""
-    from oracle import kqr_oracle as O
+def oracle_matvec_seconds(wl, budget_s: float = CPU_SAMPLE_SECONDS, seed: int = 0):
+    """Seconds for one full FP64 oracle K.v on this workload, projected from a
+    timed multi-core run of the oracle's C product (all host cores) over a
+    random row sample sized to about ``budget_s``.  Returns (seconds per full
+    product, rows sampled, seconds measured, threads)."""
+    from oracle import native as N
 
     rng = np.random.default_rng(seed)
-    idx = rng.choice(wl.n, size=min(rows, wl.n), replace=False)
     v = rng.standard_normal(wl.n)
+    probe = rng.choice(wl.n, size=min(wl.n, 64 * N.threads()), replace=False)
     t0 = time.perf_counter()
-    O.kmatvec(wl.X, v, wl.kind, wl.gamma, rows=idx)
+    N.kmatvec(wl.X, v, wl.kind, wl.gamma, rows=probe)
+    per_row = (time.perf_counter() - t0) / probe.size
+    rows = int(min(wl.n, max(probe.size, budget_s / max(per_row, 1e-12))))
+    idx = rng.choice(wl.n, size=rows, replace=False)
+    t0 = time.perf_counter()
+    N.kmatvec(wl.X, v, wl.kind, wl.gamma, rows=idx)
     dt = time.perf_counter() - t0
-    return dt * wl.n / idx.size, idx.size, dt
+    return dt * wl.n / rows, rows, dt, N.threads()
+
+
+def oracle_subsample_solve(wl, rows: int, tol: float, seed: int = 0):
+    """The oracle's full two-phase solve (Alg. 1 then Alg. 2/3, exact dense
+    FP64 solves) of the problem restricted to a random subsample of ``rows``
+    points of the workload.  Returns (seconds, eta_kkt reached, rows)."""
+    from oracle import kqr_oracle as O
+    from oracle import native as N
+
+    idx = np.sort(np.random.default_rng(seed).choice(wl.n, size=min(rows, wl.n), replace=False))
+    X, y = wl.X[idx], wl.y[idx]
+    t0 = time.perf_counter()
+    K = N.gram(X, X, wl.kind, wl.gamma)
+    res = O.solve_dense(K, y, wl.tau, wl.lam, tol=tol)
+    return time.perf_counter() - t0, max(res["kkt"]["eta_kkt"], res["kkt"]["eta_gap"]), idx.size
+
+
+def device_sm_count() -> int:
+    try:
+        import torch
+
+        return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        return SM_COUNT_FALLBACK
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -177,26 +209,38 @@ def bench_config(wl, args, world: int) -> dict:
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores.  Each step is a bounded
+    sample of the workload that the oracle completes: its full two-phase solve
+    (Alg. 1, Alg. 2/3, dense FP64) of the problem on a random subsample of
+    REF_SUBSAMPLE_ROWS points.  ``value`` is the measured seconds of one such
+    solve; the projection of one full-size solve's Gram products is reported
+    beside it, labelled as a projection."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import native as N
+
     wl = workload(args)
-    times = []
-    rows = 64 if wl.n >= 100000 else max(8, min(wl.n, 2000))
+    times, reached = [], []
     for i in range(args.warmup + args.steps):
-        per_mv, nrows, dt = oracle_matvec_seconds(wl, rows=rows, seed=i)
-        est = per_mv * REF_PRODUCTS_PER_SOLVE
+        dt, kkt, rows = oracle_subsample_solve(wl, REF_SUBSAMPLE_ROWS, args.tol, seed=i)
         if i >= args.warmup:
-            times.append(est)
+            times.append(dt)
+            reached.append(kkt)
     value = statistics.mean(times)
-    sample = (f"FP64 numpy oracle K.v on {rows} random rows of the workload per step, scaled by n/rows to one "
-              f"product and by {REF_PRODUCTS_PER_SOLVE} Gram products per solve")
+    per_mv, nrows, dt_mv, threads = oracle_matvec_seconds(wl, budget_s=min(CPU_SAMPLE_SECONDS, 5.0))
+    sample = (f"oracle full solve (Alg. 1 then Alg. 2/3, exact dense FP64 solves, K from its definition) of the "
+              f"problem on a random {rows}-point subsample of the workload, to max(eta_kkt, eta_gap) <= {args.tol:g} "
+              f"(reached {max(reached):.1e}); {threads} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": bench_config(wl, args, int(os.environ.get("WORLD_SIZE", "1"))),
-            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "full_size_projection": {
+                "kind": "projection", "unit": "s per FP64 K.v at full size", "value": per_mv,
+                "sample": f"oracle C K.v on {nrows} random rows ({dt_mv:.1f} s, {threads} threads), scaled by n/rows"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -308,24 +352,34 @@ def run_ours(args):
     # the single-vector products form each off-diagonal tile once: n(n+1)/2 entries,
     # each with two FFMAs (row and column sums)
     entries = float(n) * float(n + 1) / 2.0
-    sym_extra = 1
+    sm_count = device_sm_count()
+    sm_mhz = clk.get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK
     roofline = None
     if n32 > 0:
         avg_s = ms32 / n32 / 1e3
         if wl.kind == "laplacian":
-            ops_per_entry = 2 * p + 1 + sym_extra   # FADD + FADD|.| per feature; FFMA with v_j (and v_i)
+            ops_per_entry = 2 * p + 2               # FADD + FADD|.| per feature; FFMA with v_j and with v_i
             flops_per_entry = 3 * p + 4             # sub, abs, add per feature; scale, exp, multiply, add
         else:
-            ops_per_entry = p + 3 + sym_extra
+            ops_per_entry = p + 4
             flops_per_entry = 2 * p + 5
-        peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # Top/s, FP32 pipe lane-ops
+        peak = sm_count * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12         # Top/s, FP32 pipe lane operations
         achieved = entries * ops_per_entry / avg_s / 1e12
+        flop_peak = 2.0 * peak                                               # FFMA = 2 flops per lane and clock
+        flop_achieved = entries * flops_per_entry / avg_s / 1e12
         traffic = SYM_LAPLACIAN_TRAFFIC.get((n, p)) if wl.kind == "laplacian" else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
-                    "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": "gram_f32_sym_kernel (FP32 Gram tiles, symmetric)",
+                    "traffic": traffic, "traffic_unit": "bytes per launch",
+                    "kernel": "gram_f32_sym_kernel (FP32 Gram tiles, symmetric)",
                     "launches": n32, "avg_ms": ms32 / n32, "entries_per_launch": entries,
-                    "kv_tflops_effective": float(n) * n * flops_per_entry / avg_s / 1e12,
-                    "peak_basis": "152 SM x 128 FP32 lanes x 2070 MHz (derived, not measured)"}
+                    "work_per_entry": f"{ops_per_entry} FP32-pipe lane operations (FADD, FADD|.| per feature; "
+                                      f"two FFMAs for the row and column sums)",
+                    "peak_basis": f"{sm_count} SMs (device query) x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:g} MHz "
+                                  f"(max SM clock sampled by nvidia-smi); derived from unit counts and clocks",
+                    "flop_convention": {
+                        "achieved": flop_achieved, "peak": flop_peak, "unit": "TFLOP/s", "frac": flop_achieved / flop_peak,
+                        "flops_per_entry": flops_per_entry, "entries": "n(n+1)/2 formed per launch",
+                        "peak_basis": "SMs x 128 lanes x 2 flops (FFMA) x clock"}}
     hp = {"launches": nhp, "avg_ms": (mshp / nhp) if nhp else None}
 
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -340,12 +394,13 @@ def run_ours(args):
                       "core_builds": last["core_builds"],
                       "eta_gap": last["eta_gap"], "wall_s": t_wall, "setup_s": sum(setup_ms) / 1e3 / args.steps}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per_mv, nrows, dt = oracle_matvec_seconds(wl, rows=96 if n >= 100000 else min(n, 2000))
+        per_mv, nrows, dt, threads = oracle_matvec_seconds(wl)
         products = last["matvecs_fp32"] + last["matvecs_high"]
         line["cpu_baseline"] = {
-            "value": per_mv * products, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 numpy oracle K.v on {nrows} random rows ({dt:.1f} s), scaled by n/rows to one product "
-                       f"and by the {products} Gram products this solve used; set-up and O(n) work not counted")}
+            "value": per_mv * products, "unit": "s", "cores": threads, "kind": "projection", "source": "oracle",
+            "sample": (f"oracle C FP64 K.v (OpenMP, {threads} threads) on {nrows} random rows, {dt:.1f} s measured, "
+                       f"scaled by n/rows to one product ({per_mv:.1f} s) and by the {products} Gram products this "
+                       f"solve used; set-up and O(n) work not counted, so a lower bound on the oracle's solve")}
     prob.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

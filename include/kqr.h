@@ -214,12 +214,34 @@ kqr_status kqr_kmatvec_dev(kqr_handle* h, const double* V, double* U, int64_t m,
  * exceeds 32 MiB is rejected with KQR_INVALID_ARG and a message giving the
  * sizes (about n <= 500000 rows at m = 8).  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call shares the one array and each call
- * overwrites it completely, so two calls that overlap on the GPU (on different
- * streams, or different handles of the same device) race and both results are
- * undefined: serialise them.  Enqueues on `stream` (NULL: the handle's) and
- * returns without synchronising. */
+ * before any stream capture.  The address is cached per device and CUDA
+ * context: after cudaDeviceReset the next call looks it up again (handles
+ * created before the reset are invalid anyway).  Every call shares the one
+ * array and each call overwrites it completely, so two calls that overlap on
+ * the GPU (on different streams, or different handles of the same device) race
+ * and both results are undefined: serialise them.  Enqueues on `stream` (NULL:
+ * the handle's) and returns without synchronising, so it cannot report a Gram
+ * kernel that gave up a bounded wait on a tile copy (U is then incomplete):
+ * after synchronising that stream, call kqr_check_device. */
 kqr_status kqr_kmatvec_fp32_noalloc_dev(kqr_handle* h, const double* V, double* U, int64_t m, void* stream);
+
+/* Reads the handle's device error word, which a kernel sets when it gives up
+ * a bounded wait on a tile copy or an MMA (kqr_status
+ * KQR_DEVICE_WAIT_TIMEOUT); the results of that call are then incomplete.
+ * The *_dev calls and kqr_kmatvec_fp32_noalloc_dev return without
+ * synchronising, so they cannot report this themselves: synchronise the stream
+ * they were enqueued on, then call this.  Returns KQR_DEVICE_WAIT_TIMEOUT (and
+ * clears the word) if a kernel gave up since the last check, else KQR_OK.
+ * Synchronises the device (blocking copy).  No counterpart in the paper. */
+kqr_status kqr_check_device(kqr_handle* h);
+
+/* Exercises the timeout path of the kernels' bounded waits: one CTA waits on
+ * a barrier that nothing completes, gives up after max_polls polls (1 ..
+ * 2^20) and records the timeout in the device error word, exactly as a Gram
+ * kernel does when a tile copy never lands; no copy or MMA is in flight.  A
+ * following kqr_check_device returns KQR_DEVICE_WAIT_TIMEOUT.  Synchronises.
+ * For tests of the error path; no counterpart in the paper. */
+kqr_status kqr_test_bounded_wait(kqr_handle* h, uint32_t max_polls);
 
 /* Projection, Jacobian and gradient of the ALM subproblem (eq. (2.3), Sec. 2.2,
  * eq. (3.1)), device vectors of length n:
@@ -244,7 +266,10 @@ kqr_status kqr_precond_apply_dev(kqr_handle* h, const double* Ldiag, double gam,
 /* Preconditioned CG (Sec. 3) for (K + gam 1 1^T + diag(Ldiag)) x = b with the
  * handle's preconditioner kind, FP32 Gram products, from x = 0, until the
  * recursive residual satisfies ||r|| <= tol or maxit iterations.  b, x device.
- * *iters (nullable) receives the iteration count.  Synchronises. */
+ * *iters (nullable) receives the iteration count.  Returns KQR_NOT_CONVERGED
+ * (x holds the last iterate) when CG stopped before meeting tol: at maxit, or
+ * at a non-positive curvature p^T A p <= 0 (FP32 rounding on a numerically
+ * low-rank K; the message says which).  Synchronises. */
 kqr_status kqr_pcg_dev(kqr_handle* h, const double* Ldiag, double gam, const double* b, double* x,
                        double tol, int32_t maxit, int32_t* iters, void* stream);
 

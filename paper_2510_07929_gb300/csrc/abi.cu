@@ -600,6 +600,9 @@ kqr_status kqr_pcg_dev(kqr_handle* kh, const double* Ldiag, double gam, const do
   s = pcg(h, L, Lpre, gam, b, x, nullptr, false, tol, maxit, &it, st);
   if (iters) *iters = it;
   if (s == KQR_OK && cudaStreamSynchronize(st) != cudaSuccess) return fail(h, KQR_CUDA_ERROR, "pcg sync");
+  if (s == KQR_OK && !h->cg_met)
+    return fail(h, KQR_NOT_CONVERGED, h->cg_truncated ? "CG stopped at a non-positive curvature p^T A p <= 0"
+                                                      : "CG reached maxit before the tolerance");
   return s;
 }
 
@@ -624,6 +627,29 @@ kqr_status kqr_kkt(kqr_handle* kh, const double* alpha, const double* v, double 
   cudaStreamSynchronize(st);
   dev_free(h, buf);
   return s;
+}
+
+kqr_status kqr_check_device(kqr_handle* kh) {
+  if (!kh) return KQR_INVALID_ARG;
+  Handle* h = &kh->h;
+  if (!h->err_flag) return fail(h, KQR_INVALID_ARG, "handle has no device state");
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "read device error word");
+  if (!flag) return KQR_OK;
+  if ((e = cudaMemset(h->err_flag, 0, sizeof(int))) != cudaSuccess) return cuda_fail(h, e, "clear device error word");
+  return fail(h, KQR_DEVICE_WAIT_TIMEOUT, "a kernel gave up a bounded wait; its results are incomplete");
+}
+
+kqr_status kqr_test_bounded_wait(kqr_handle* kh, uint32_t max_polls) {
+  if (!kh) return KQR_INVALID_ARG;
+  Handle* h = &kh->h;
+  if (!h->err_flag) return fail(h, KQR_INVALID_ARG, "handle has no device state");
+  if (max_polls < 1 || max_polls > (1u << 20)) return fail(h, KQR_INVALID_ARG, "max_polls must be in [1, 2^20]");
+  cudaError_t e = launch_wait_probe(h, max_polls, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "bounded-wait probe");
+  return KQR_OK;
 }
 
 kqr_status kqr_refactor(kqr_handle* kh, const double* pivot_uniforms) {

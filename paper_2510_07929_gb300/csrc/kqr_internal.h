@@ -149,6 +149,8 @@ struct Handle {
   size_t prof_used[2] = {0, 0};
   int num_sms = 0;
   int64_t cg_truncations = 0;         // CG runs stopped at a non-positive curvature
+  bool cg_met = false;                // the last CG run met its residual tolerance
+  bool cg_truncated = false;          // the last CG run stopped at a non-positive curvature
   double dres_mean = 1.0;             // RPCholesky's mean residual diagonal (before the floor)
   bool cg_high_on = false;            // this solve's CG products are FP64-class
   BatchData* batch = nullptr;         // set for batched-product handles (batch.cu)
@@ -197,6 +199,8 @@ cudaError_t box_grad(Handle* h, const double* alpha, const double* z, const doub
 cudaError_t scale_vec(Handle* h, double* out, const double* x, double s, int64_t n, cudaStream_t st);
 cudaError_t axpy_vec(Handle* h, double* y, const double* x, double a, int64_t n, cudaStream_t st);
 cudaError_t fill_L(Handle* h, double* L, double base, const double* dres, int64_t n, cudaStream_t st);
+// Bounded wait on an mbarrier nothing arrives on (the wait-timeout path; kqr_test_bounded_wait).
+cudaError_t launch_wait_probe(Handle* h, uint32_t max_polls, cudaStream_t st);
 
 // ---- preconditioner (woodbury.cu, rpchol.cu) -------------------------------------
 kqr_status precond_build(Handle* h, const double* Ldiag, double gam, cudaStream_t st);

@@ -21,15 +21,46 @@ cudaError_t gram_f32_scratch(Handle* h, const double* V, double* U, int m, unsig
 
 static std::mutex g_scratch_mu;
 static unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
+static unsigned long long g_scratch_ctx[kMaxDevices] = {0};
 
-// Device address of g_noalloc_scratch on `device` (the current device).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique ID of the current CUDA context (cuCtxGetId), 0 if unavailable.  A
+// device reset destroys the primary context and the next one gets a new ID,
+// which invalidates the cached address below.
+static unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (CtxGetCurrentFn)p;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS) return id;
+  return 0;
+}
+
+// Device address of g_noalloc_scratch on `device` (the current device), looked
+// up with cudaGetSymbolAddress once per device and context.
 static cudaError_t scratch_address(int device, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[device]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_addr[device] || g_scratch_ctx[device] != ctx) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[device] = static_cast<unsigned char*>(p);
+    g_scratch_ctx[device] = ctx;
   }
   *out = g_scratch_addr[device];
   return cudaSuccess;

@@ -94,6 +94,8 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
     CK(reduce(h, RED_SUM, ra, n, h->scal + S_SUMP, st));
     CK(op_residual(h, r, b, x, Kx, gam, h->scal + S_SUMP, L, n, st));
   }
+  h->cg_met = false;
+  h->cg_truncated = false;
   RedArgs rn;
   rn.a = r;
   CK(reduce(h, RED_NORM2, rn, n, h->scal + S_RR, st));
@@ -102,6 +104,7 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
   if (!std::isfinite(rr)) return fail(h, KQR_BREAKDOWN, "CG: non-finite residual");
   if (std::sqrt(rr) <= tol) {
     if (iters) *iters = 0;
+    h->cg_met = true;
     return KQR_OK;
   }
   CK(precond_apply(h, Lpre, r, zz, h->scal + S_RZ, st));
@@ -137,6 +140,7 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
         ++it;
       }
       h->cg_truncations++;
+      h->cg_truncated = true;
       break;
     }
     CK(put(h, S_A, rz / pAp, st));
@@ -148,7 +152,10 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
       if (iters) *iters = it;
       return fail(h, KQR_BREAKDOWN, "CG: non-finite residual");
     }
-    if (std::sqrt(rr) <= tol) break;
+    if (std::sqrt(rr) <= tol) {
+      h->cg_met = true;
+      break;
+    }
     CK(precond_apply(h, Lpre, r, zz, h->scal + S_RZ, st));
     CK(fetch(h, S_RZ, 1, st));
     const double rz_new = h->scal_host[S_RZ];

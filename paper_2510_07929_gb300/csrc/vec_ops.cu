@@ -7,6 +7,7 @@
 // Reductions are deterministic: each block writes its partial sums, and the
 // last block to finish adds the partials in block order.
 #include "kqr_internal.h"
+#include "ptx.cuh"
 
 namespace kqr {
 
@@ -266,6 +267,24 @@ cudaError_t box_grad(Handle* h, const double* alpha, const double* z, const doub
   const double sa = h->scal_host[S_RED0 + 12];
   return run_reduce<1>(h, FBoxGrad{alpha, z, Kalpha, y, dres, beta, sigma, tau, lam, eps, sa, v, S, grad, Ldiag, Lpre},
                        n, h->scal + S_RED0 + 13, st);
+}
+
+// One CTA waits, bounded by max_polls, on an mbarrier that nothing arrives on:
+// the timeout path of mbar_wait_bounded, which records kErrWaitTimeout in the
+// error word.  No copy or MMA is in flight, so the early exit leaves nothing
+// behind.
+__global__ void wait_probe_kernel(int* err, uint32_t max_polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    (void)mbar_wait_bounded(&bar, 0u, err, max_polls);
+  }
+}
+
+cudaError_t launch_wait_probe(Handle* h, uint32_t max_polls, cudaStream_t st) {
+  wait_probe_kernel<<<1, 32, 0, st>>>(h->err_flag, max_polls);
+  return post(h);
 }
 
 }  // namespace kqr

@@ -74,6 +74,8 @@ SIGNATURES = {
     "kqr_kmatvec": (ctypes.c_int, [_P, _DP, _DP, _I64, ctypes.c_int]),
     "kqr_kmatvec_dev": (ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, _P]),
     "kqr_kmatvec_fp32_noalloc_dev": (ctypes.c_int, [_P, _P, _P, _I64, _P]),
+    "kqr_check_device": (ctypes.c_int, [_P]),
+    "kqr_test_bounded_wait": (ctypes.c_int, [_P, ctypes.c_uint32]),
     "kqr_box_grad_dev": (ctypes.c_int, [_P, _P, _P, _P, _D, _D, _D, _D, _D, _P, _P, _P, _P, _DP, _P]),
     "kqr_precond_apply_dev": (ctypes.c_int, [_P, _P, _D, _P, _P, _P]),
     "kqr_pcg_dev": (ctypes.c_int, [_P, _P, _D, _P, _P, _D, _I32, ctypes.POINTER(_I32), _P]),
@@ -233,6 +235,20 @@ class Problem:
         m = 1 if V.dim() == 1 else V.shape[1]
         self._check(self._lib.kqr_kmatvec_dev(self._h, _tptr(V), _tptr(U), m, prec, _stream_ptr(stream)))
         return U
+
+    def kmatvec_noalloc_dev(self, V, U, stream=None):
+        """FP32 U = K V through the entry point that allocates no device memory
+        (kqr_kmatvec_fp32_noalloc_dev); V, U contiguous CUDA float64 tensors."""
+        m = 1 if V.dim() == 1 else V.shape[1]
+        self._check(self._lib.kqr_kmatvec_fp32_noalloc_dev(self._h, _tptr(V), _tptr(U), m, _stream_ptr(stream)))
+        return U
+
+    def check_device(self) -> int:
+        """kqr_check_device: OK, or DEVICE_WAIT_TIMEOUT if a kernel gave up a bounded wait."""
+        return int(self._lib.kqr_check_device(self._h))
+
+    def test_bounded_wait(self, max_polls: int):
+        self._check(self._lib.kqr_test_bounded_wait(self._h, max_polls))
 
     def box_grad_dev(self, alpha, z, Kalpha, beta, sigma, tau, lam, eps, v=None, S=None, grad=None, Ldiag=None,
                      stream=None):

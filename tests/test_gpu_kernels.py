@@ -3,6 +3,10 @@
 Tolerances: FP32 Gram products within 1e-5 of max|K v| (FP32 entries, about
 1e-7 relative each); the FP64-class product within 1e-12 of sum_j |K_ij v_j|
 per row; FP64 vector kernels within 1e-11 relative."""
+import json
+import math
+import os
+
 import numpy as np
 import pytest
 
@@ -257,3 +261,46 @@ def test_invalid_arguments_are_rejected(K_):
             assert e.value.status == K_.INVALID_ARG
         with pytest.raises(K_.KQRError):
             prob.kmatvec(np.zeros((50, 9)))
+
+
+def test_kkt_residuals_three_point_golden(K_):
+    """The hand-computed Sec. 4 residuals of tests/golden/kkt_three_point.json
+    (z != 0, alpha != v, 1^T alpha != 0) through kqr_kkt."""
+    c = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "kkt_three_point.json")))
+    env = {"sqrt": math.sqrt, "log": math.log}
+    with K_.Problem(np.array(c["x"]), np.array(c["y"]), c["kind"], eval(c["gamma"], env), rank0=2) as prob:
+        got = prob.kkt(np.array(c["alpha"]), np.array(c["v"]), c["beta"], np.array(c["z"]), c["tau"], c["lam"])
+    for key, expr in c["expected"].items():
+        assert got[key] == pytest.approx(eval(expr, env), rel=1e-12), key
+
+
+def test_pcg_reports_unconverged(K_):
+    """kqr_pcg_dev stopped by maxit before its tolerance returns
+    KQR_NOT_CONVERGED (x holds the last iterate), not KQR_OK."""
+    import torch
+
+    wl = W.lap_large(n=900, p=10)
+    rng = np.random.default_rng(6)
+    L = np.full(wl.n, 1e-4)
+    b = rng.standard_normal(wl.n)
+    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma, precond=2) as prob:
+        x = torch.zeros(wl.n, dtype=torch.float64, device="cuda")
+        with pytest.raises(K_.KQRError) as e:
+            prob.pcg_dev(torch.from_numpy(L).cuda(), 1e-4, torch.from_numpy(b).cuda(), x, 1e-14, 2)
+        assert e.value.status == K_.NOT_CONVERGED and "maxit" in str(e.value)
+        assert np.all(np.isfinite(x.cpu().numpy())) and float(x.abs().sum()) > 0
+
+
+def test_bounded_wait_timeout_is_reported(K_):
+    """A kernel that gives up a bounded wait (here on a barrier nothing
+    completes, with no copy in flight) leaves the timeout in the device error
+    word; kqr_check_device reports it once and the context stays usable."""
+    wl = W.rbf_small(n=300)
+    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma) as prob:
+        assert prob.check_device() == K_.OK
+        prob.test_bounded_wait(64)
+        assert prob.check_device() == K_.DEVICE_WAIT_TIMEOUT
+        assert prob.check_device() == K_.OK
+        v = W.random_vectors(wl.n, seed=2)
+        ref = O.kmatvec(wl.X, v, wl.kind, wl.gamma)
+        assert np.max(np.abs(prob.kmatvec(v) - ref)) <= 1e-5 * np.max(np.abs(ref))

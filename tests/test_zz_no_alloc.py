@@ -3,13 +3,16 @@
 It serves callers that cannot allocate device memory when they need a
 product (a fully pre-reserved memory pool, an allocator callback, a loop that
 must not synchronise on cudaMalloc): its scratch is a static device array.
-This file is collected last so that a run stopping at its first failure has
-already run every other test; it also passes on its own in a fresh process."""
-import ctypes
-
+Checked against the oracle (1e-5 of max|K V|, the FP32 contract) and against
+the allocating entry point, for both kernels (the RBF path of this entry point
+is the CUDA-core kernel, the allocating one defaults to tcgen05), two calls in
+a row sharing the static array.  This file is collected last so that a run
+stopping at its first failure has already run every other test; it also
+passes on its own in a fresh process."""
 import numpy as np
 import pytest
 
+from oracle import kqr_oracle as O
 from paper_2510_07929_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -29,27 +32,26 @@ def K_():
     return kqr
 
 
-def _noalloc(K_, prob, V, U, m):
-    return K_.lib().kqr_kmatvec_fp32_noalloc_dev(prob._h, ctypes.c_void_p(V.data_ptr()),
-                                                 ctypes.c_void_p(U.data_ptr()), m, None)
-
-
-def test_noalloc_product_matches_allocating_entry_point_twice(K_):
+@pytest.mark.parametrize("kind", ["laplacian", "rbf"])
+def test_noalloc_product_matches_oracle_and_allocating_entry_point(K_, kind):
     import torch
 
-    wl = W.lap_large(n=3001, p=20, seed=2)
+    wl = W.lap_large(n=3001, p=20, seed=2) if kind == "laplacian" else W.rbf_mid(n=3001, p=20, seed=2)
     with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma, rank0=8) as prob:
-        for call, m in enumerate((3, 1)):          # two calls in a row share the static scratch
-            V = torch.from_numpy(W.random_vectors(wl.n, m, seed=20 + call)).cuda().contiguous()
+        for call, m in enumerate((3, 1, 8)):       # calls in a row share the static scratch
+            Vh = W.random_vectors(wl.n, m, seed=20 + call)
+            V = torch.from_numpy(Vh).cuda().contiguous()
             U_ref = torch.empty_like(V)
             U = torch.full_like(V, float("nan"))
             prob.kmatvec_dev(V, U_ref, K_.PREC_FP32)
-            assert _noalloc(K_, prob, V, U, m) == K_.OK
+            prob.kmatvec_noalloc_dev(V, U)
             torch.cuda.synchronize()
-            ref = U_ref.cpu().numpy()
+            assert prob.check_device() == K_.OK
+            ref = O.kmatvec(wl.X, Vh, wl.kind, wl.gamma)
             got = U.cpu().numpy()
             assert np.all(np.isfinite(got))
-            assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+            assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref)), (m, np.max(np.abs(got - ref)))
+            assert np.max(np.abs(got - U_ref.cpu().numpy())) <= 1e-5 * np.max(np.abs(ref))
 
 
 def test_noalloc_product_rejects_oversized_problems(K_):
@@ -62,6 +64,7 @@ def test_noalloc_product_rejects_oversized_problems(K_):
     with K_.Problem(X, y, "rbf", 0.5, rank0=2) as prob:
         V = torch.zeros((n, 8), dtype=torch.float64, device="cuda")
         U = torch.zeros_like(V)
-        st = _noalloc(K_, prob, V, U, 8)
-        assert st == K_.INVALID_ARG
-        assert b"bytes of scratch" in K_.lib().kqr_last_error(prob._h)
+        with pytest.raises(K_.KQRError) as e:
+            prob.kmatvec_noalloc_dev(V, U)
+        assert e.value.status == K_.INVALID_ARG
+        assert "bytes of scratch" in str(e.value)
