@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override n (testing only)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--rank0", type=int, default=1024, help="initial RPCholesky rank (library default: ceil(sqrt n))")
+    ap.add_argument("--gram-store", type=int, default=0,
+                    help="CG products from a stored K: 0 on the fly (the headline workload's stated form), "
+                         "1 always, 2 when it fits (library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verbose", action="store_true")
@@ -270,7 +273,7 @@ def run_ours(args):
     from paper_2510_07929_gb300 import kqr
 
     wl = workload(args, seed=rank)
-    opts = dict(rank0=args.rank0, verbose=1 if args.verbose else 0)
+    opts = dict(rank0=args.rank0, verbose=1 if args.verbose else 0, gram_store=args.gram_store)
     prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, **opts)
     stream = torch.cuda.Stream()
     prob.set_stream(stream)
@@ -338,7 +341,8 @@ def run_ours(args):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with kqr.Problem(Xp.numpy(), yp.numpy(), wl.kind, wl.gamma, rank0=args.rank0) as p2:
+            with kqr.Problem(Xp.numpy(), yp.numpy(), wl.kind, wl.gamma, rank0=args.rank0,
+                             gram_store=args.gram_store) as p2:
                 alpha, beta, kkt2, _ = p2.solve(wl.tau, wl.lam, args.tol)
             torch.cuda.synchronize()
             e2e_s.append(time.perf_counter() - t0)
@@ -419,10 +423,13 @@ def run_gram(args):
     from paper_2510_07929_gb300 import kqr
 
     wl = workload(args)
-    prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, rank0=args.rank0)
+    t0 = time.perf_counter()
+    prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, rank0=args.rank0, gram_store=args.gram_store)
+    create_s = time.perf_counter() - t0
     V = torch.from_numpy(np.random.default_rng(0).standard_normal(wl.n)).cuda()
     U = torch.empty_like(V)
-    out = {"mode": "gram", "config": {"workload": describe(wl, args)}}
+    out = {"mode": "gram", "config": {"workload": describe(wl, args), "gram_store": args.gram_store},
+           "create_s": create_s}
     for name, prec in (("fp32", kqr.PREC_FP32), ("high", kqr.PREC_HIGH)):
         prob.kmatvec_dev(V, U, prec)
         torch.cuda.synchronize()
@@ -430,6 +437,12 @@ def run_gram(args):
         for _ in range(args.matvecs):
             prob.kmatvec_dev(V, U, prec)
         cnt, ms = prob.profile_read(0 if prec == kqr.PREC_FP32 else 1)
+        if prec == kqr.PREC_FP32 and cnt == 0:
+            cnt, ms = prob.profile_read(2)
+            name = "fp32_stored"
+            stored_bytes = (wl.n + 127) // 128 * ((wl.n + 127) // 128 + 1) // 2 * 65536
+            out["stored_bytes"] = stored_bytes
+            out["stored_gbs"] = stored_bytes / (ms / max(cnt, 1) / 1e3) / 1e9
         prob.profile(False)
         out[name] = {"launches": cnt, "avg_ms": ms / max(cnt, 1)}
     prob.close()

@@ -20,8 +20,10 @@
  * (representer form, Sec. 1).
  *
  * Every step of the solve runs in CUDA kernels on the current device.  Kernel
- * matrices are never stored: their entries are formed in tiles inside the
- * Gram-product kernels.
+ * matrix entries are formed in tiles inside the Gram-product kernels; the
+ * FP32 products inside CG stream a stored copy of K's upper triangle instead
+ * when it fits in device memory (options.gram_store), since each entry is
+ * then formed once rather than once per product.
  *
  * Conventions for every function below:
  *   - Host pointers ("host") are read or written before the call returns; the
@@ -136,6 +138,12 @@ typedef struct kqr_options {
   int32_t cg_high;               /* CG products: 0 FP32; 1 FP64-class; 2 FP64-class when K is numerically
                                     low-rank at FP32 resolution (RPCholesky's mean residual diagonal below
                                     2^-24 n), where FP32 products cannot resolve most of the spectrum */
+  int32_t gram_store;            /* FP32 single-vector products (the CG products) from a stored K:
+                                    0 never (entries formed on the fly in tiles every product);
+                                    1 always (kqr_create fills the packed upper triangle of K as
+                                    128 x 128 FP32 tiles, (T (T + 1) / 2) * 64 KB with T = ceil(n / 128),
+                                    and returns KQR_OOM if it does not fit); 2 (default) when those
+                                    bytes are at most half the free device memory at kqr_create */
 } kqr_options;
 
 /* Counters and final residuals of a solve (Sec. 4 definitions). */
@@ -149,6 +157,7 @@ typedef struct kqr_info {
   double eta_p, eta_d, eta_c, eta_kkt, eta_gap, obj_p, obj_d;
   double sigma_final;
   double seconds;                      /* wall-clock of the solve */
+  int32_t gram_stored;                 /* 1: the FP32 products streamed a stored K (options.gram_store) */
 } kqr_info;
 
 typedef struct kqr_handle kqr_handle;
@@ -293,8 +302,9 @@ kqr_status kqr_refactor(kqr_handle* h, const double* pivot_uniforms);
 /* Instrumentation (no counterpart in the paper).  kqr_profile(h, 1) resets
  * and enables CUDA-event timing of the Gram tile kernels on the handle's
  * stream; kqr_profile(h, 0) disables it.  kqr_profile_read returns, for
- * kernel_id 0 (FP32 Gram tiles) or 1 (FP64-class Gram tiles), the number of
- * launches and their summed device time in milliseconds since the last reset.
+ * kernel_id 0 (FP32 Gram tiles), 1 (FP64-class Gram tiles) or 2 (stored-K
+ * product), the number of launches and their summed device time in
+ * milliseconds since the last reset.
  * Reading synchronises the handle's stream. */
 kqr_status kqr_profile(kqr_handle* h, int32_t enable);
 kqr_status kqr_profile_read(kqr_handle* h, int32_t kernel_id, int64_t* launches, double* total_ms);

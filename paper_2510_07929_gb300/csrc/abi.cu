@@ -188,9 +188,10 @@ static void free_all(Handle* h) {
                   h->Linv, h->part, h->v32, h->vec_pool, h->scal, h->red_counter, h->red_part, h->err_flag,
                   h->st_alpha, h->st_v, h->st_z, h->sym_units, h->tc_hi, h->tc_lo, h->tc_bf};
   for (void* b : bufs) dev_free(h, b);
+  kstore_free(h);
   batch_free(h);
   if (h->scal_host) cudaFreeHost(h->scal_host);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 3; ++k) {
     for (cudaEvent_t e : h->prof_ev[k]) cudaEventDestroy(e);
     h->prof_ev[k].clear();
   }
@@ -327,6 +328,8 @@ static kqr_status create(Handle* h, const double* X, const double* y, int64_t n,
         !make_tmap(&h->tm_hl, h->hl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ldn, p))
       return fail(h, KQR_CUDA_ERROR, "cuTensorMapEncodeTiled failed for the fixed-point layout");
   }
+  kqr_status ks = kstore_setup(h);
+  if (ks != KQR_OK) return ks;
   return rpcholesky_setup(h, uniforms);
 }
 
@@ -373,6 +376,7 @@ void kqr_default_options(kqr_options* o) {
   o->rbf_tensor_cores = 1;
   o->verbose = 0;
   o->cg_high = 0;
+  o->gram_store = 2;
 }
 
 void kqr_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*), void* ctx) {
@@ -735,7 +739,7 @@ kqr_status kqr_batch_kmatmul(kqr_handle* kh, const double* V, double* U, int64_t
 kqr_status kqr_profile(kqr_handle* kh, int32_t enable) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
-  h->prof_used[0] = h->prof_used[1] = 0;
+  h->prof_used[0] = h->prof_used[1] = h->prof_used[2] = 0;
   h->profile = enable != 0;
   return KQR_OK;
 }
@@ -743,7 +747,7 @@ kqr_status kqr_profile(kqr_handle* kh, int32_t enable) {
 kqr_status kqr_profile_read(kqr_handle* kh, int32_t kernel_id, int64_t* launches, double* total_ms) {
   if (!kh) return KQR_INVALID_ARG;
   Handle* h = &kh->h;
-  if (kernel_id < 0 || kernel_id > 1) return fail(h, KQR_INVALID_ARG, "kernel_id must be 0 or 1");
+  if (kernel_id < 0 || kernel_id > 2) return fail(h, KQR_INVALID_ARG, "kernel_id must be 0, 1 or 2");
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(h, KQR_CUDA_ERROR, "profile sync");
   double tot = 0.0;
   const size_t pairs = h->prof_used[kernel_id] / 2;

@@ -262,6 +262,7 @@ static void pick_splits(Handle* h, int resident_per_sm, int* splits, int* tps) {
 }
 
 cudaError_t gram_f32(Handle* h, const double* V, double* U, int m, const GramEpilogue* ep, cudaStream_t st) {
+  if (m == 1 && h->kstore) return gram_stored(h, V, U, ep, st);
   if (h->kind == KQR_RBF && h->opt.rbf_tensor_cores) return gram_rbf_tc(h, V, U, m, true, ep, st);
   if (m == 1 && h->opt.symmetric_gram) return gram_f32_sym(h, V, U, ep, st);
   const int M = m <= 1 ? 1 : (m <= 2 ? 2 : (m <= 4 ? 4 : 8));

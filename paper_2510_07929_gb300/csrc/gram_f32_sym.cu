@@ -270,3 +270,26 @@ cudaError_t gram_f32_sym(Handle* h, const double* V, double* U, const GramEpilog
 }
 
 }  // namespace kqr
+
+namespace kqr {
+
+// v -> FP32 copy and zeroed FP32 accumulator (and 1^T v into *sum_out if given),
+// for products that accumulate with atomics (symmetric tiles, stored K).
+cudaError_t sym_prep(Handle* h, const double* V, float* v32, float* acc, double* sum_out, cudaStream_t st) {
+  cudaError_t e;
+  if (sum_out && (e = cudaMemsetAsync(sum_out, 0, sizeof(double), st)) != cudaSuccess) return e;
+  sym_prep_kernel<<<grid_for(h->ldn), 256, 0, st>>>(V, v32, acc, h->n, h->ldn, sum_out);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+// out = acc (+ the CG operator's terms of g), as at the end of gram_f32_sym.
+cudaError_t sym_finish(Handle* h, const float* acc, double* U, const GramEpilogue& g, cudaStream_t st) {
+  cudaError_t e;
+  if (g.dot_out && (e = cudaMemsetAsync(g.dot_out, 0, sizeof(double), st)) != cudaSuccess) return e;
+  sym_finish_kernel<<<grid_for(h->n), 256, 0, st>>>(acc, h->n, U, g);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace kqr

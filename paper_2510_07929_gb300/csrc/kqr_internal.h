@@ -64,6 +64,12 @@ cudaError_t gram_f32_sym(Handle* h, const double* V, double* U, const GramEpilog
 cudaError_t gram_high(Handle* h, const double* V, double* U, int m, cudaStream_t st);
 // Laplacian m = 1 FP64-class product with each off-diagonal tile formed once (gram_high_sym.cu).
 cudaError_t gram_high_sym(Handle* h, const double* V, double* U, cudaStream_t st);
+// Stored-K product (gram_stored.cu): kstore_setup fills the packed upper-triangle tiles
+// when options.gram_store asks for it and they fit; gram_stored streams them (m = 1).
+size_t kstore_bytes(int64_t ldn);
+kqr_status kstore_setup(Handle* h);
+void kstore_free(Handle* h);
+cudaError_t gram_stored(Handle* h, const double* V, double* U, const GramEpilogue* ep, cudaStream_t st);
 // Column s of K in FP64 (RPCholesky).
 
 struct Handle {
@@ -145,8 +151,8 @@ struct Handle {
   std::string err;
   // Event timing of the Gram tile kernels (kqr_profile): pairs per kernel id.
   bool profile = false;
-  std::vector<cudaEvent_t> prof_ev[2];
-  size_t prof_used[2] = {0, 0};
+  std::vector<cudaEvent_t> prof_ev[3];
+  size_t prof_used[3] = {0, 0, 0};
   int num_sms = 0;
   int64_t cg_truncations = 0;         // CG runs stopped at a non-positive curvature
   bool cg_met = false;                // the last CG run met its residual tolerance
@@ -154,6 +160,12 @@ struct Handle {
   double dres_mean = 1.0;             // RPCholesky's mean residual diagonal (before the floor)
   bool cg_high_on = false;            // this solve's CG products are FP64-class
   BatchData* batch = nullptr;         // set for batched-product handles (batch.cu)
+
+  // Stored upper-triangle tiles of K (gram_stored.cu; options.gram_store), or null.
+  float* kstore = nullptr;
+  size_t kstore_bytes = 0;
+  int4* kstore_sched = nullptr;       // per-CTA (first tile, end tile, I, J) of the product
+  int kstore_grid = 0;
 };
 
 kqr_status fail(Handle* h, kqr_status s, const std::string& msg);

@@ -282,6 +282,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
   h->cg_high_on = !mixed && (o.cg_high == 1 || (o.cg_high == 2 && h->dres_mean < std::ldexp((double)n, -24)));
   kqr_info inf{};
   inf.rank = h->r;
+  inf.gram_stored = h->kstore ? 1 : 0;
   const int64_t builds0 = h->core_builds;
   const int64_t trunc0 = h->cg_truncations;
   double res[7] = {0, 0, 0, 0, 0, 0, 0};

@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
         ("core_reuse_rtol", ctypes.c_double),
         ("time_limit_s", ctypes.c_double), ("phase1_only", ctypes.c_int32),
         ("symmetric_gram", ctypes.c_int32), ("rbf_tensor_cores", ctypes.c_int32), ("cg_tf32", ctypes.c_int32),
-        ("verbose", ctypes.c_int32), ("cg_high", ctypes.c_int32),
+        ("verbose", ctypes.c_int32), ("cg_high", ctypes.c_int32), ("gram_store", ctypes.c_int32),
     ]
 
 
@@ -53,6 +53,7 @@ class Info(ctypes.Structure):
         ("eta_p", ctypes.c_double), ("eta_d", ctypes.c_double), ("eta_c", ctypes.c_double),
         ("eta_kkt", ctypes.c_double), ("eta_gap", ctypes.c_double), ("obj_p", ctypes.c_double),
         ("obj_d", ctypes.c_double), ("sigma_final", ctypes.c_double), ("seconds", ctypes.c_double),
+        ("gram_stored", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

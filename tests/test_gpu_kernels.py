@@ -43,8 +43,11 @@ GRAM_CASES = [("rbf", 2, 1), ("laplacian", 2, 1), ("rbf", 129, 3), ("laplacian",
               ("laplacian", 700, 64), ("rbf", 257, 64)]
 
 
-PATHS = {"sym_tc": dict(symmetric_gram=1, rbf_tensor_cores=1), "plain_tc": dict(symmetric_gram=0, rbf_tensor_cores=1),
-         "sym_cuda": dict(symmetric_gram=1, rbf_tensor_cores=0), "plain_cuda": dict(symmetric_gram=0, rbf_tensor_cores=0)}
+PATHS = {"sym_tc": dict(symmetric_gram=1, rbf_tensor_cores=1, gram_store=0),
+         "plain_tc": dict(symmetric_gram=0, rbf_tensor_cores=1, gram_store=0),
+         "sym_cuda": dict(symmetric_gram=1, rbf_tensor_cores=0, gram_store=0),
+         "plain_cuda": dict(symmetric_gram=0, rbf_tensor_cores=0, gram_store=0),
+         "stored": dict(gram_store=1)}
 
 
 @pytest.mark.parametrize("path", list(PATHS))
@@ -54,6 +57,8 @@ def test_gram_products_match_oracle(K_, kind, n, p, path):
     tcgen05 (three TF32 terms) or on FP32 CUDA cores."""
     if kind == "laplacian" and path.endswith("_cuda"):
         pytest.skip("the tensor-core switch applies to the RBF kernel only")
+    if path == "stored" and n > 1000:
+        pytest.skip("stored-K parity at larger n: test_stored_gram_matches_oracle")
     wl = _data(kind, n, p)
     with K_.Problem(wl.X, wl.y, kind, wl.gamma, **PATHS[path]) as prob:
         for m in (1, 3, 8):
@@ -144,7 +149,7 @@ def test_gram_full_size_sampled_rows(K_):
     rows = np.random.default_rng(5).choice(wl.n, 24, replace=False)
     ref = O.kmatvec(wl.X, v, wl.kind, wl.gamma, rows=rows)
     absref = O.kmatvec(wl.X, np.abs(v), wl.kind, wl.gamma, rows=rows)
-    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma, rank0=16) as prob:
+    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma, rank0=16, gram_store=0) as prob:
         uhp = prob.kmatvec(v, K_.PREC_HIGH)
         u32 = prob.kmatvec(v, K_.PREC_FP32)
     assert np.max(np.abs(uhp[rows] - ref) / absref) <= 1e-12
@@ -304,3 +309,42 @@ def test_bounded_wait_timeout_is_reported(K_):
         v = W.random_vectors(wl.n, seed=2)
         ref = O.kmatvec(wl.X, v, wl.kind, wl.gamma)
         assert np.max(np.abs(prob.kmatvec(v) - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("kind,n,p", [("rbf", 2000, 10), ("laplacian", 2000, 50), ("rbf", 20000, 20),
+                                      ("laplacian", 20000, 50), ("rbf", 130, 3), ("laplacian", 257, 4)])
+def test_stored_gram_matches_oracle(K_, kind, n, p):
+    """The stored-K product (packed upper-triangle tiles filled once, then
+    streamed; options.gram_store = 1) against the FP64 oracle (the C form at
+    n = 20000) and against the on-the-fly symmetric tiles, over two products
+    in a row on one handle."""
+    from oracle import native as N
+
+    wl = _data(kind, n, p, seed=3)
+    with K_.Problem(wl.X, wl.y, kind, wl.gamma, gram_store=1, rank0=8) as prob, \
+            K_.Problem(wl.X, wl.y, kind, wl.gamma, gram_store=0, rank0=8) as fly:
+        for seed in (1, 2):
+            v = W.random_vectors(n, seed=seed)
+            ref = N.kmatvec(wl.X, v, kind, wl.gamma)
+            u = prob.kmatvec(v, K_.PREC_FP32)
+            assert np.max(np.abs(u - ref)) <= 1e-5 * np.max(np.abs(ref)), np.max(np.abs(u - ref))
+            assert np.max(np.abs(u - fly.kmatvec(v, K_.PREC_FP32))) <= 1e-5 * np.max(np.abs(ref))
+        prob.profile(True)
+        prob.kmatvec(v, K_.PREC_FP32)
+        launches, ms = prob.profile_read(2)
+        assert launches == 1 and ms > 0
+
+
+def test_stored_gram_falls_back_when_not_asked_or_too_large(K_):
+    """gram_store = 0 never stores; the automatic mode stores small problems."""
+    wl = _data("rbf", 500, 4)
+    with K_.Problem(wl.X, wl.y, "rbf", wl.gamma, gram_store=0) as prob:
+        prob.kmatvec(W.random_vectors(500))
+        prob.profile(True)
+        prob.kmatvec(W.random_vectors(500))
+        assert prob.profile_read(2)[0] == 0
+        _, _, _, info = prob.solve(0.5, 1e-2, 1e-6)
+        assert info["gram_stored"] == 0
+    with K_.Problem(wl.X, wl.y, "rbf", wl.gamma) as prob:
+        _, _, _, info = prob.solve(0.5, 1e-2, 1e-6)
+        assert info["gram_stored"] == 1

@@ -55,16 +55,19 @@ def check_against_oracle(wl, alpha, beta, v, z, kkt, tol=1e-6):
     return ref
 
 
+@pytest.mark.parametrize("gram_store", [0, 1])
 @pytest.mark.parametrize("name,n,tau", [("rbf_small", 2000, 0.5), ("rbf_small", 1531, 0.1),
                                         ("lap_large", 2500, 0.25), ("rbf_mid", 2200, 0.9),
                                         ("yuan2006", 1800, 0.1)])
-def test_solve_matches_oracle(K_, name, n, tau):
+def test_solve_matches_oracle(K_, name, n, tau, gram_store):
+    """CG products formed on the fly (gram_store = 0) or streamed from a stored K."""
     gen = W.GENERATORS[name]
     wl = gen(n=n, tau=tau)
     # solved to 1e-7 so that the 1e-6 objective parity holds with margin: a
     # 1e-6 infeasibility moves the dual objective by ~ ||y - K a / lambda|| 1e-6
-    alpha, beta, v, z, kkt, info = gpu_solve(K_, wl, tol=1e-7)
+    alpha, beta, v, z, kkt, info = gpu_solve(K_, wl, tol=1e-7, gram_store=gram_store)
     assert info["status"] == K_.OK and info["phase1_iters"] >= 1
+    assert info["gram_stored"] == gram_store
     check_against_oracle(wl, alpha, beta, v, z, kkt)
 
 
@@ -154,7 +157,7 @@ def full_size(K_):
     """One n = 200000 Laplacian solve (the benchmark's workload), shared by the
     full-size tests."""
     wl = W.lap_large()
-    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma) as prob:
+    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma, gram_store=0) as prob:
         alpha, beta, kkt, info = prob.solve(wl.tau, wl.lam, 1e-6)
         v, z = prob.state()
     return wl, alpha, beta, v, z, kkt, info
