@@ -288,7 +288,11 @@ def run_ours(args):
         _, _, kkt, info = step()
         infos.append(info)
     barrier()
-    prob.profile(True)
+    # kernel timing (CUDA events around every Gram launch) is kept off for small
+    # problems: it disables the CUDA graphs of the CG iterations there
+    profiled = wl.n > 32768
+    if profiled:
+        prob.profile(True)
     launches0 = prob.launches
     clocks = ClockSampler(local)
     clocks.start()

@@ -190,6 +190,11 @@ static void free_all(Handle* h) {
   for (void* b : bufs) dev_free(h, b);
   kstore_free(h);
   batch_free(h);
+  for (auto& g : h->cg_graph)
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
   if (h->scal_host) cudaFreeHost(h->scal_host);
   for (int k = 0; k < 3; ++k) {
     for (cudaEvent_t e : h->prof_ev[k]) cudaEventDestroy(e);

@@ -197,7 +197,7 @@ __global__ void gram_reduce_kernel(const float* __restrict__ part, int splits, i
     double s = 0.0;
     for (int sp = 0; sp < splits; ++sp) s += (double)part[((size_t)sp * ldn + row) * M + c];
     if (ep.raw_out) ep.raw_out[idx] = s;
-    if (ep.L) s += ep.gam * sump + ep.L[row] * ep.pvec[row];
+    if (ep.L) s += (ep.gam_dev ? *ep.gam_dev : ep.gam) * sump + ep.L[row] * ep.pvec[row];
     out[idx] = s;
     if (ep.dot_out) dot += ep.pvec[row] * s;
   }

@@ -187,7 +187,7 @@ __global__ void sym_finish_kernel(const float* __restrict__ acc, int64_t n, doub
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = (double)acc[i];
     if (ep.raw_out) ep.raw_out[i] = s;
-    if (ep.L) s += ep.gam * sump + ep.L[i] * ep.pvec[i];
+    if (ep.L) s += (ep.gam_dev ? *ep.gam_dev : ep.gam) * sump + ep.L[i] * ep.pvec[i];
     out[i] = s;
     if (ep.dot_out) dot += ep.pvec[i] * s;
   }

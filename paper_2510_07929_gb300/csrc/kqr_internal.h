@@ -45,6 +45,7 @@ void dev_free(Handle* h, void* p);
 // with dot_out (device, nullable) accumulating sum_i p[i] out[i].
 struct GramEpilogue {
   double gam = 0.0;
+  const double* gam_dev = nullptr; // device scalar read instead of gam when set (graph-captured CG)
   const double* sum_p = nullptr;   // device scalar 1^T p
   const double* L = nullptr;       // device diagonal
   const double* pvec = nullptr;    // device vector p (FP64)
@@ -161,6 +162,15 @@ struct Handle {
   bool cg_high_on = false;            // this solve's CG products are FP64-class
   BatchData* batch = nullptr;         // set for batched-product handles (batch.cu)
 
+  // CUDA graphs of a block of CG iterations (solver.cu), one per solution vector
+  // (Phase I alpha, Phase II direction d); rebuilt when a pointer they captured changes.
+  struct CgGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key;
+    int64_t launches = 0;              // kernel launches one graph launch stands for
+  } cg_graph[2];
+  bool cg_graphs_off = false;         // capture failed once: enqueue directly from then on
+
   // Stored upper-triangle tiles of K (gram_stored.cu; options.gram_store), or null.
   float* kstore = nullptr;
   size_t kstore_bytes = 0;
@@ -196,7 +206,9 @@ cudaError_t vec_copy(Handle* h, double* dst, const double* src, int64_t n, cudaS
 // y = a * x + y (device scalar a read from *a_dev, scaled by sgn)
 cudaError_t cg_update(Handle* h, double* x, double* Kx, double* r, const double* p, const double* Kp,
                       const double* Ap, const double* a_dev, int64_t n, double* rr_out, cudaStream_t st);
-cudaError_t cg_direction(Handle* h, double* p, const double* z, const double* beta_dev, int64_t n, cudaStream_t st);
+// p = z + beta p (beta read from beta_dev); a non-zero *stop_dev (nullable) skips it.
+cudaError_t cg_direction(Handle* h, double* p, const double* z, const double* beta_dev, const double* stop_dev,
+                         int64_t n, cudaStream_t st);
 cudaError_t op_residual(Handle* h, double* r, const double* b, const double* x, const double* Kx, double gam,
                         const double* sum_x, const double* L, int64_t n, cudaStream_t st);
 cudaError_t admm_rhs(Handle* h, double* b, const double* y, double beta, const double* z, const double* v,
@@ -245,7 +257,12 @@ enum Vec {
 inline double* vec(Handle* h, Vec v) { return h->vec_pool + (size_t)v * h->ldn; }
 
 // Scalar slots in scal / scal_host.
-enum Scal { S_RED0 = 0, S_SUMP = 16, S_PAP = 17, S_A = 18, S_BETA = 19, S_RR = 20, S_RZ = 21, S_COUNT = 32 };
+enum Scal {
+  S_RED0 = 0, S_SUMP = 16, S_PAP = 17, S_A = 18, S_BETA = 19, S_RR = 20, S_RZ = 21,
+  // device-resident CG control (solver.cu): new rz, status, iterations, tol^2, pending status, maxit
+  S_RZN = 22, S_CGST = 23, S_CGITS = 24, S_TOL2 = 25, S_PEND = 26, S_MAXIT = 27, S_GAM = 28,
+  S_COUNT = 32
+};
 
 // Launch configuration for element-wise kernels.
 // ---- batched multi-RHS products (batch.cu) ---------------------------------------

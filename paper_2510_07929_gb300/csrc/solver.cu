@@ -75,6 +75,76 @@ static cudaError_t high_operator(Handle* h, const double* p, double* Ap, double*
   return reduce(h, RED_DOT, rd, h->n, dot, st);
 }
 
+// ---- device-resident CG control ---------------------------------------------------
+// CG's scalars live in device slots; small single-thread kernels compute the step
+// lengths and the stopping test, so the host reads one status word per block of
+// iterations instead of three blocking copies per iteration.  Status (S_CGST):
+// 0 running, 1 met tol, 2 stopped at a non-positive curvature, 3 non-finite, 4 maxit.
+enum CgState { CG_RUN = 0, CG_MET = 1, CG_TRUNC = 2, CG_NONFINITE = 3, CG_MAXIT = 4 };
+
+// a = rz / pAp, or the truncation step, into S_A; the pending status into S_PEND.
+__global__ void cg_alpha_kernel(double* __restrict__ s) {
+  if ((int)s[S_CGST] != CG_RUN) {
+    s[S_A] = 0.0;
+    s[S_PEND] = s[S_CGST];
+    return;
+  }
+  const double pAp = s[S_PAP];
+  if (!isfinite(pAp)) {
+    s[S_A] = 0.0;
+    s[S_PEND] = CG_NONFINITE;
+  } else if (!(pAp > 0.0)) {
+    // The operator is positive definite; a non-positive curvature is FP32 rounding in
+    // directions whose eigenvalues lie below the product's accuracy (a numerically
+    // low-rank K).  Truncate: keep x, or at the first step take the preconditioned
+    // residual itself (a Newton step with the preconditioner as the Hessian model).
+    s[S_A] = s[S_CGITS] == 0.0 ? 1.0 : 0.0;
+    s[S_PEND] = CG_TRUNC;
+  } else {
+    s[S_A] = s[S_RZ] / pAp;
+    s[S_PEND] = CG_RUN;
+  }
+}
+
+// After the update: iteration count and stopping test.
+__global__ void cg_check_kernel(double* __restrict__ s) {
+  if ((int)s[S_CGST] != CG_RUN) return;
+  const int pend = (int)s[S_PEND];
+  if (s[S_A] != 0.0) s[S_CGITS] += 1.0;
+  const double rr = s[S_RR];
+  int st = pend;
+  if (st == CG_RUN) {
+    if (!isfinite(rr)) st = CG_NONFINITE;
+    else if (rr <= s[S_TOL2]) st = CG_MET;
+    else if (s[S_CGITS] >= s[S_MAXIT]) st = CG_MAXIT;
+  }
+  s[S_CGST] = st;
+}
+
+// beta = rz_new / rz and rz <- rz_new while running.
+__global__ void cg_beta_kernel(double* __restrict__ s) {
+  if ((int)s[S_CGST] != CG_RUN) return;
+  const double rzn = s[S_RZN];
+  s[S_BETA] = rzn / s[S_RZ];
+  s[S_RZ] = rzn;
+}
+
+__global__ void cg_init_kernel(double* __restrict__ s, double tol2, double maxit, double gam) {
+  s[S_CGST] = CG_RUN;
+  s[S_CGITS] = 0.0;
+  s[S_TOL2] = tol2;
+  s[S_MAXIT] = maxit;
+  s[S_GAM] = gam;
+}
+
+// CG iterations per host status read: one per product when a product costs far more
+// than a host round trip, more when the products are cheap (small n).
+static int cg_block(Handle* h) {
+  if (h->n <= 8192) return 16;
+  if (h->n <= 32768) return 4;
+  return 1;
+}
+
 kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const double* b, double* x, double* Kx,
                bool warm, double tol, int maxit, int* iters, cudaStream_t st, bool lowprec) {
   const int64_t n = h->n;
@@ -83,7 +153,9 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
   double* p = vec(h, V_P);
   double* Ap = vec(h, V_AP);
   double* Kp = vec(h, V_KP);
-  int it = 0;
+  double* s = h->scal;
+  h->cg_met = false;
+  h->cg_truncated = false;
   if (!warm) {
     CK(vec_fill(h, x, 0.0, n, st));
     if (Kx) CK(vec_fill(h, Kx, 0.0, n, st));
@@ -91,79 +163,126 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
   } else {
     RedArgs ra;
     ra.a = x;
-    CK(reduce(h, RED_SUM, ra, n, h->scal + S_SUMP, st));
-    CK(op_residual(h, r, b, x, Kx, gam, h->scal + S_SUMP, L, n, st));
+    CK(reduce(h, RED_SUM, ra, n, s + S_SUMP, st));
+    CK(op_residual(h, r, b, x, Kx, gam, s + S_SUMP, L, n, st));
   }
-  h->cg_met = false;
-  h->cg_truncated = false;
   RedArgs rn;
   rn.a = r;
-  CK(reduce(h, RED_NORM2, rn, n, h->scal + S_RR, st));
+  CK(reduce(h, RED_NORM2, rn, n, s + S_RR, st));
+  CK(precond_apply(h, Lpre, r, zz, s + S_RZ, st));
+  CK(vec_copy(h, p, zz, n, st));
+  cg_init_kernel<<<1, 1, 0, st>>>(s, tol * tol, (double)maxit, gam);
+  h->launches++;
+  CK(cudaGetLastError());
   CK(fetch(h, S_RR, 1, st));
-  double rr = h->scal_host[S_RR];
-  if (!std::isfinite(rr)) return fail(h, KQR_BREAKDOWN, "CG: non-finite residual");
-  if (std::sqrt(rr) <= tol) {
+  const double rr0 = h->scal_host[S_RR];
+  if (!std::isfinite(rr0)) return fail(h, KQR_BREAKDOWN, "CG: non-finite residual");
+  if (std::sqrt(rr0) <= tol) {
     if (iters) *iters = 0;
     h->cg_met = true;
     return KQR_OK;
   }
-  CK(precond_apply(h, Lpre, r, zz, h->scal + S_RZ, st));
-  CK(vec_copy(h, p, zz, n, st));
-  CK(fetch(h, S_RZ, 1, st));
-  double rz = h->scal_host[S_RZ];
-  while (it < maxit) {
-    GramEpilogue ep;
-    ep.gam = gam;
-    ep.sum_p = h->scal + S_SUMP;
-    ep.L = L;
-    ep.pvec = p;
-    ep.dot_out = h->scal + S_PAP;
-    ep.raw_out = Kp;
-    if (h->cg_high_on && !lowprec) CK(high_operator(h, p, Ap, Kp, L, gam, h->scal + S_SUMP, h->scal + S_PAP, st));
-    else if (lowprec) CK(gram_rbf_tc(h, p, Ap, 1, false, &ep, st));
-    else CK(gram_f32(h, p, Ap, 1, &ep, st));
-    CK(fetch(h, S_PAP, 1, st));
-    const double pAp = h->scal_host[S_PAP];
-    if (!std::isfinite(pAp)) {
-      KS(check_device_flag(h, st));
-      if (iters) *iters = it;
-      return fail(h, KQR_BREAKDOWN, "CG: p^T A p = " + std::to_string(pAp));
+  const int block = cg_block(h);
+  // One block of CG iterations, every scalar on the device.
+  auto enqueue_block = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < block && e == cudaSuccess; ++j) {
+      GramEpilogue ep;
+      ep.gam = gam;
+      ep.gam_dev = s + S_GAM;
+      ep.sum_p = s + S_SUMP;
+      ep.L = L;
+      ep.pvec = p;
+      ep.dot_out = s + S_PAP;
+      ep.raw_out = Kp;
+      if (h->cg_high_on && !lowprec) e = high_operator(h, p, Ap, Kp, L, gam, s + S_SUMP, s + S_PAP, st);
+      else if (lowprec) e = gram_rbf_tc(h, p, Ap, 1, false, &ep, st);
+      else e = gram_f32(h, p, Ap, 1, &ep, st);
+      if (e != cudaSuccess) break;
+      cg_alpha_kernel<<<1, 1, 0, st>>>(s);
+      h->launches++;
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      if ((e = cg_update(h, x, Kx, r, p, Kp, Ap, s + S_A, n, s + S_RR, st)) != cudaSuccess) break;
+      cg_check_kernel<<<1, 1, 0, st>>>(s);
+      h->launches++;
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      if ((e = precond_apply(h, Lpre, r, zz, s + S_RZN, st)) != cudaSuccess) break;
+      cg_beta_kernel<<<1, 1, 0, st>>>(s);
+      h->launches++;
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      e = cg_direction(h, p, zz, s + S_BETA, s + S_CGST, n, st);
     }
-    if (!(pAp > 0.0)) {
-      // The operator is positive definite; a non-positive curvature is FP32 rounding in
-      // directions whose eigenvalues lie below the product's accuracy (a numerically
-      // low-rank K).  Truncate: keep x, or at the first step take the preconditioned
-      // residual itself (a Newton step with the preconditioner as the Hessian model).
-      if (it == 0) {
-        CK(put(h, S_A, 1.0, st));
-        CK(cg_update(h, x, Kx, r, p, Kp, Ap, h->scal + S_A, n, h->scal + S_RR, st));
-        ++it;
+    return e;
+  };
+  // With several iterations per status read, the block is captured once as a CUDA
+  // graph and relaunched (kernel arguments are pointers and device scalars only;
+  // gam is read from S_GAM).  A graph is captured only after a block has run
+  // directly with the same buffers, so that every buffer the products use exists
+  // before capture; later calls with the same buffers launch it from the start.
+  const bool graphs = block > 1 && !h->profile && !h->cg_graphs_off && !(h->cg_high_on && !lowprec);
+  Handle::CgGraph* g = nullptr;
+  std::vector<const void*> key;
+  if (graphs) {
+    g = &h->cg_graph[x == vec(h, V_ALPHA) ? 0 : 1];
+    key = {x, Kx, b, L, Lpre, h->v32, h->part, h->F32, h->core, h->Linv, h->tvec, h->kstore, h->sym_units,
+           h->tc_hi, reinterpret_cast<const void*>((intptr_t)(h->r * 8 + (lowprec ? 1 : 0) + 2 * h->opt.precond)),
+           reinterpret_cast<const void*>((intptr_t)block), reinterpret_cast<const void*>(st)};
+  }
+  int state = CG_RUN, it = 0;
+  bool first = true;
+  while (state == CG_RUN) {
+    if (graphs && !first && (!g->exec || g->key != key)) {
+      // capture the block (relaxed mode: the launch helpers set kernel attributes)
+      cudaGraph_t graph = nullptr;
+      const int64_t l0 = h->launches;
+      cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+      cudaError_t e2 = e == cudaSuccess ? enqueue_block() : e;
+      if (e == cudaSuccess) e = cudaStreamEndCapture(st, &graph);
+      const int64_t nodes = h->launches - l0;
+      h->launches = l0;
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess && g->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(g->exec, graph, &info) != cudaSuccess) {
+          cudaGetLastError();
+          cudaGraphExecDestroy(g->exec);
+          g->exec = nullptr;
+        }
       }
-      h->cg_truncations++;
-      h->cg_truncated = true;
-      break;
+      if (e == cudaSuccess && !g->exec) e = cudaGraphInstantiate(&g->exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        // leave graphs off for this handle and carry on with direct launches
+        cudaGetLastError();
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+        h->cg_graphs_off = true;
+      } else {
+        g->key = key;
+        g->launches = nodes;
+      }
     }
-    CK(put(h, S_A, rz / pAp, st));
-    CK(cg_update(h, x, Kx, r, p, Kp, Ap, h->scal + S_A, n, h->scal + S_RR, st));
-    CK(fetch(h, S_RR, 1, st));
-    rr = h->scal_host[S_RR];
-    ++it;
-    if (!std::isfinite(rr)) {
-      if (iters) *iters = it;
-      return fail(h, KQR_BREAKDOWN, "CG: non-finite residual");
+    if (graphs && g->exec && g->key == key && !h->cg_graphs_off) {
+      CK(cudaGraphLaunch(g->exec, st));
+      h->launches += g->launches;
+    } else {
+      CK(enqueue_block());
     }
-    if (std::sqrt(rr) <= tol) {
-      h->cg_met = true;
-      break;
-    }
-    CK(precond_apply(h, Lpre, r, zz, h->scal + S_RZ, st));
-    CK(fetch(h, S_RZ, 1, st));
-    const double rz_new = h->scal_host[S_RZ];
-    CK(put(h, S_BETA, rz_new / rz, st));
-    CK(cg_direction(h, p, zz, h->scal + S_BETA, n, st));
-    rz = rz_new;
+    first = false;
+    CK(fetch(h, S_RR, S_CGITS - S_RR + 1, st));
+    state = (int)h->scal_host[S_CGST];
+    it = (int)h->scal_host[S_CGITS];
   }
   if (iters) *iters = it;
+  if (state == CG_NONFINITE) {
+    KS(check_device_flag(h, st));
+    return fail(h, KQR_BREAKDOWN, "CG: non-finite curvature or residual");
+  }
+  if (state == CG_TRUNC) {
+    h->cg_truncations++;
+    h->cg_truncated = true;
+  }
+  h->cg_met = state == CG_MET;
   KS(check_device_flag(h, st));
   return KQR_OK;
 }

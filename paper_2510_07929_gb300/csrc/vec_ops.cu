@@ -154,7 +154,10 @@ struct FCgUpdate {
   }
 };
 
-__global__ void cg_direction_kernel(double* p, const double* z, const double* beta_dev, int64_t n) {
+// p = z + beta p, unless the device-resident CG status (stop_dev, nullable) says it stopped.
+__global__ void cg_direction_kernel(double* p, const double* z, const double* beta_dev, const double* stop_dev,
+                                    int64_t n) {
+  if (stop_dev && *stop_dev != 0.0) return;
   const double b = *beta_dev;
   GRID_LOOP(i, n) p[i] = z[i] + b * p[i];
 }
@@ -231,8 +234,9 @@ cudaError_t cg_update(Handle* h, double* x, double* Kx, double* r, const double*
                       const double* Ap, const double* a_dev, int64_t n, double* rr_out, cudaStream_t st) {
   return run_reduce<1>(h, FCgUpdate{x, Kx, r, p, Kp, Ap, a_dev}, n, rr_out, st);
 }
-cudaError_t cg_direction(Handle* h, double* p, const double* z, const double* beta_dev, int64_t n, cudaStream_t st) {
-  cg_direction_kernel<<<grid_for(n), 256, 0, st>>>(p, z, beta_dev, n);
+cudaError_t cg_direction(Handle* h, double* p, const double* z, const double* beta_dev, const double* stop_dev,
+                         int64_t n, cudaStream_t st) {
+  cg_direction_kernel<<<grid_for(n), 256, 0, st>>>(p, z, beta_dev, stop_dev, n);
   return post(h);
 }
 cudaError_t op_residual(Handle* h, double* r, const double* b, const double* x, const double* Kx, double gam,
