@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verbose", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "gram", "precision", "path", "grad", "batch"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "gram", "precision", "path", "grad", "batch", "grid"],
                     help="gram: time --matvecs FP32 and FP64-class Gram products only (kernel profiling)")
     ap.add_argument("--matvecs", type=int, default=3)
     ap.add_argument("--ncu-window", action="store_true",
@@ -73,6 +73,12 @@ def parse():
     ap.add_argument("--batch-p-in-smem", action="store_true",
                     help="--mode batch: stage the Gram tile through shared memory instead of tensor memory")
     ap.add_argument("--time-limit", type=float, default=600.0, help="per-solve wall-clock limit (s) in the study modes")
+    ap.add_argument("--grid-problems", type=int, default=64, help="--mode grid: number of problems")
+    ap.add_argument("--grid-nmax", type=int, default=20000, help="--mode grid: n_b ~ U{1000..nmax}")
+    ap.add_argument("--grid-side", type=int, default=8, help="--mode grid: taus x lambdas = side x side pairs")
+    ap.add_argument("--grid-workers", type=int, default=4, help="--mode grid: problems solved at a time")
+    ap.add_argument("--grid-seq-sample", type=int, default=32,
+                    help="--mode grid: pairs solved one at a time through kqr_solve for the comparison")
     return ap.parse_args()
 
 
@@ -693,8 +699,79 @@ def run_batch(args):
     return 0
 
 
+def grid_workload(problems: int, nmax: int, side: int, seed: int = 0):
+    """The batched workload: problems with n_b ~ U{1000..nmax} (seed 0), each the
+    rbf_small recipe at p = 8 from seed 1000 + b (x ~ U[0,1]^8, RBF gamma = 1/8),
+    and side taus in [0.05, 0.95] x side lambdas log-spaced in [1e-5, 1e-1]."""
+    from paper_2510_07929_gb300 import workloads as W
+
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(1000, nmax + 1, size=problems)
+    wls = [W.rbf_small(n=int(n), p=8, seed=1000 + b) for b, n in enumerate(sizes)]
+    taus, lams = np.meshgrid(np.linspace(0.05, 0.95, side), np.logspace(-5, -1, side), indexing="ij")
+    return wls, taus.ravel(), lams.ravel()
+
+
+def run_grid(args):
+    """Grid solves on the batched workload: every problem's (tau, lambda) pairs
+    through kqr_solve_grid_batch (the pairs of a problem share their Gram
+    products), against the same pairs solved one at a time through kqr_solve on
+    the same handles (all of them when --grid-seq-sample covers the grid, else a
+    random sample of pairs, whose mean time is scaled to the grid and labelled a
+    projection).  CG products: FP64-class where the kernel is numerically
+    low-rank at FP32 resolution (options.cg_high = 2), as on this smooth kernel."""
+    import torch
+
+    from paper_2510_07929_gb300 import build
+
+    build.build()
+    from paper_2510_07929_gb300 import kqr
+
+    wls, taus, lams = grid_workload(args.grid_problems, args.grid_nmax, args.grid_side)
+    tol = args.tol
+    t0 = time.perf_counter()
+    probs = [kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, cg_high=2, time_limit_s=args.time_limit) for wl in wls]
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out = kqr.solve_grid_batch(probs, taus, lams, tol=tol, workers=args.grid_workers)
+    t_grid = time.perf_counter() - t0
+    statuses = np.concatenate([o[3] for o in out])
+    worst = float(max(np.max(o[2]) for o in out))
+    pairs = len(wls) * taus.size
+    rng = np.random.default_rng(1)
+    sample = [(int(b), int(c)) for b, c in zip(rng.integers(0, len(wls), size=pairs),
+                                                rng.integers(0, taus.size, size=pairs))]
+    full = args.grid_seq_sample >= pairs
+    if full:
+        sample = [(b, c) for b in range(len(wls)) for c in range(taus.size)]
+    else:
+        sample = sample[:args.grid_seq_sample]
+    seq = []
+    for b, c in sample:
+        t1 = time.perf_counter()
+        _, _, kkt, info = probs[b].solve(float(taus[c]), float(lams[c]), tol, allow_not_converged=True)
+        seq.append(time.perf_counter() - t1)
+    t_seq = sum(seq) if full else float(np.mean(seq)) * pairs
+    for p in probs:
+        p.close()
+    res = {"mode": "grid",
+           "workload": f"{len(wls)} RBF problems, n_b ~ U{{1000..{args.grid_nmax}}} (seed 0), p=8, gamma=1/8, "
+                       f"{args.grid_side} taus in [0.05, 0.95] x {args.grid_side} lambdas in [1e-5, 1e-1], tol {tol:g}",
+           "sum_n": int(sum(w.n for w in wls)), "pairs": pairs, "create_s": t_create, "grid_s": t_grid,
+           "grid_status_counts": {str(k): int(v) for k, v in zip(*np.unique(statuses, return_counts=True))},
+           "grid_worst_kkt": worst,
+           "sequential": {"kind": "measured" if full else "projection", "pairs_timed": len(seq),
+                          "seconds": t_seq, "mean_s_per_pair": float(np.mean(seq))},
+           "speedup": t_seq / t_grid}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "grid":
+        return run_grid(args)
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "grad":

@@ -135,9 +135,10 @@ typedef struct kqr_options {
   int32_t cg_tf32;               /* RBF only, 1: CG products in TF32 on tcgen05 (one term), each linear solve
                                     iteratively refined against FP32 residuals to the same tolerance */
   int32_t verbose;               /* 1: one line per outer iteration on stderr */
-  int32_t cg_high;               /* CG products: 0 FP32; 1 FP64-class; 2 FP64-class when K is numerically
-                                    low-rank at FP32 resolution (RPCholesky's mean residual diagonal below
-                                    2^-24 n), where FP32 products cannot resolve most of the spectrum */
+  int32_t cg_high;               /* CG products: 0 FP32; 1 FP64-class; 2 (default) FP64-class when K is
+                                    numerically low-rank at FP32 resolution: from the start when
+                                    RPCholesky's mean residual diagonal is below 2^-24 n, and from the
+                                    first CG run that stops at a rounding-level curvature on */
   int32_t gram_store;            /* FP32 single-vector products (the CG products) from a stored K:
                                     0 never (entries formed on the fly in tiles every product);
                                     1 always (kqr_create fills the packed upper triangle of K as
@@ -158,6 +159,7 @@ typedef struct kqr_info {
   double sigma_final;
   double seconds;                      /* wall-clock of the solve */
   int32_t gram_stored;                 /* 1: the FP32 products streamed a stored K (options.gram_store) */
+  int32_t cg_high_used;                /* 1: the CG products were FP64-class at the end (options.cg_high) */
 } kqr_info;
 
 typedef struct kqr_handle kqr_handle;
@@ -188,6 +190,33 @@ kqr_status kqr_create(const double* X, const double* y, int64_t n, int64_t p, kq
  * iteration caps are reached.  Synchronises. */
 kqr_status kqr_solve(kqr_handle* h, double tau, double lambda, double tol,
                      double* alpha, double* beta, double* kkt, kqr_info* info);
+
+/* Solves the dual (1.3) for m pairs (taus[c], lambdas[c]), 1 <= m <= 4096, on
+ * the handle's problem, to the tolerance of kqr_solve: a grid of quantile
+ * levels and regularisation weights on one data set (Sec. 4.1 fits paths of
+ * 50 lambdas).  Every pair runs the two-phase method of kqr_solve on its own
+ * state; the pairs' Gram products are taken together, up to 8 right-hand
+ * sides per kernel launch (FP32, or FP64-class where options.cg_high says so,
+ * and always for gradients and Sec. 4 residuals), so one pass over the kernel
+ * matrix serves several pairs; a pair that has converged drops out of the
+ * shared products.  alpha (host, n x m column-major: pair c at alpha + c n),
+ * beta, kkt and status (host, m each) receive each pair's result as kqr_solve
+ * would (status[c] is that pair's kqr_status); info (nullable, m entries) its
+ * counters.  Returns KQR_OK when every pair returned KQR_OK, KQR_NOT_CONVERGED
+ * or KQR_TIMEOUT (see status), else the first failure.  Uses one host thread
+ * per pair; allocates device memory; synchronises. */
+kqr_status kqr_solve_grid(kqr_handle* h, int64_t m, const double* taus, const double* lambdas, double tol,
+                          double* alpha, double* beta, double* kkt, int32_t* status, kqr_info* info);
+
+/* kqr_solve_grid on B problems (single-problem handles hs[0..B), each created
+ * with its own X, y, kernel and gamma; sizes may differ) with the same m pairs,
+ * `workers` problems at a time (<= 0: 4), each problem's products on its own
+ * stream.  alpha (host): problem b's n_b x m column-major block at
+ * alpha + m (n_0 + ... + n_{b-1}); beta, kkt, status (host): B x m, row b for
+ * problem b.  Synchronises. */
+kqr_status kqr_solve_grid_batch(kqr_handle* const* hs, int64_t B, int64_t m, const double* taus, const double* lambdas,
+                                double tol, int32_t workers, double* alpha, double* beta, double* kkt,
+                                int32_t* status);
 
 /* After kqr_solve: copies the last iterate's consensus variable v and
  * multiplier z of (1.4)-(1.5) to host arrays of length n (either may be NULL). */

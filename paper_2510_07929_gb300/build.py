@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkqr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["abi.cu", "gram_f32.cu", "gram_high.cu", "vec_ops.cu", "precond.cu", "solver.cu", "noalloc.cu", "gram_f32_sym.cu", "gram_high_sym.cu", "gram_rbf_tc.cu", "grad.cu", "batch.cu", "gram_stored.cu"]
+SOURCES = ["abi.cu", "gram_f32.cu", "gram_high.cu", "vec_ops.cu", "precond.cu", "solver.cu", "noalloc.cu", "gram_f32_sym.cu", "gram_high_sym.cu", "gram_rbf_tc.cu", "grad.cu", "batch.cu", "gram_stored.cu", "grid.cu"]
 
 
 def nvcc() -> str:

@@ -380,7 +380,7 @@ void kqr_default_options(kqr_options* o) {
   o->symmetric_gram = 1;
   o->rbf_tensor_cores = 1;
   o->verbose = 0;
-  o->cg_high = 0;
+  o->cg_high = 2;
   o->gram_store = 2;
 }
 

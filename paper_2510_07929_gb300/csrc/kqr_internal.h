@@ -33,6 +33,7 @@ struct Allocator {
 
 struct Handle;
 struct BatchData;
+struct GridRdv;
 
 // ---- device memory ---------------------------------------------------------
 void* dev_alloc(Handle* h, size_t bytes);
@@ -157,7 +158,7 @@ struct Handle {
   int num_sms = 0;
   int64_t cg_truncations = 0;         // CG runs stopped at a non-positive curvature
   bool cg_met = false;                // the last CG run met its residual tolerance
-  bool cg_truncated = false;          // the last CG run stopped at a non-positive curvature
+  bool cg_truncated = false;          // the last CG run stopped at a non-positive (rounding-level) curvature
   double dres_mean = 1.0;             // RPCholesky's mean residual diagonal (before the floor)
   bool cg_high_on = false;            // this solve's CG products are FP64-class
   BatchData* batch = nullptr;         // set for batched-product handles (batch.cu)
@@ -170,6 +171,11 @@ struct Handle {
     int64_t launches = 0;              // kernel launches one graph launch stands for
   } cg_graph[2];
   bool cg_graphs_off = false;         // capture failed once: enqueue directly from then on
+
+  // Grid solves (grid.cu): set on the per-column clones, whose products meet in the rendezvous.
+  GridRdv* rdv = nullptr;
+  cudaEvent_t rdv_ev = nullptr;
+  int64_t grid_rounds = 0, grid_columns = 0;   // products run for grids, and columns they carried
 
   // Stored upper-triangle tiles of K (gram_stored.cu; options.gram_store), or null.
   float* kstore = nullptr;
@@ -206,9 +212,10 @@ cudaError_t vec_copy(Handle* h, double* dst, const double* src, int64_t n, cudaS
 // y = a * x + y (device scalar a read from *a_dev, scaled by sgn)
 cudaError_t cg_update(Handle* h, double* x, double* Kx, double* r, const double* p, const double* Kp,
                       const double* Ap, const double* a_dev, int64_t n, double* rr_out, cudaStream_t st);
-// p = z + beta p (beta read from beta_dev); a non-zero *stop_dev (nullable) skips it.
+// p = z + beta p (beta read from beta_dev); a non-zero *stop_dev (nullable) skips it;
+// ||p||^2 into *pp_out (device).
 cudaError_t cg_direction(Handle* h, double* p, const double* z, const double* beta_dev, const double* stop_dev,
-                         int64_t n, cudaStream_t st);
+                         int64_t n, double* pp_out, cudaStream_t st);
 cudaError_t op_residual(Handle* h, double* r, const double* b, const double* x, const double* Kx, double gam,
                         const double* sum_x, const double* L, int64_t n, cudaStream_t st);
 cudaError_t admm_rhs(Handle* h, double* b, const double* y, double beta, const double* z, const double* v,
@@ -260,7 +267,7 @@ inline double* vec(Handle* h, Vec v) { return h->vec_pool + (size_t)v * h->ldn; 
 enum Scal {
   S_RED0 = 0, S_SUMP = 16, S_PAP = 17, S_A = 18, S_BETA = 19, S_RR = 20, S_RZ = 21,
   // device-resident CG control (solver.cu): new rz, status, iterations, tol^2, pending status, maxit
-  S_RZN = 22, S_CGST = 23, S_CGITS = 24, S_TOL2 = 25, S_PEND = 26, S_MAXIT = 27, S_GAM = 28,
+  S_RZN = 22, S_CGST = 23, S_CGITS = 24, S_TOL2 = 25, S_PEND = 26, S_MAXIT = 27, S_GAM = 28, S_PP = 29,
   S_COUNT = 32
 };
 

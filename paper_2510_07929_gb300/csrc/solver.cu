@@ -51,7 +51,15 @@ static kqr_status check_device_flag(Handle* h, cudaStream_t st) {
   return KQR_OK;
 }
 
-// Ap = K p + gam (1^T p) 1 + L o p with the FP64-class product; Kp = K p; pAp into *dot.
+// K p with the FP64-class (high) or FP32 product; a grid column (kqr_solve_grid) posts it
+// to the columns' shared multi-right-hand-side product instead.
+cudaError_t grid_product(Handle* h, const double* p, double* out, bool high, cudaStream_t st);
+static cudaError_t raw_product(Handle* h, const double* p, double* out, bool high, cudaStream_t st) {
+  if (h->rdv) return grid_product(h, p, out, high, st);
+  return high ? gram_high(h, p, out, 1, st) : gram_f32(h, p, out, 1, nullptr, st);
+}
+
+// Ap = K p + gam (1^T p) 1 + L o p; Kp = K p; pAp into *dot.
 __global__ void high_op_kernel(double* __restrict__ Ap, const double* __restrict__ Kp, const double* __restrict__ p,
                                const double* __restrict__ L, const double* __restrict__ sump, double gam, int64_t n) {
   const double sg = gam * (*sump);
@@ -59,13 +67,13 @@ __global__ void high_op_kernel(double* __restrict__ Ap, const double* __restrict
     Ap[i] = Kp[i] + sg + L[i] * p[i];
 }
 
-static cudaError_t high_operator(Handle* h, const double* p, double* Ap, double* Kp, const double* L, double gam,
-                                 double* sump, double* dot, cudaStream_t st) {
+static cudaError_t op_product(Handle* h, const double* p, double* Ap, double* Kp, const double* L, double gam,
+                              double* sump, double* dot, bool high, cudaStream_t st) {
   RedArgs rs;
   rs.a = p;
   cudaError_t e = reduce(h, RED_SUM, rs, h->n, sump, st);
   if (e != cudaSuccess) return e;
-  if ((e = gram_high(h, p, Kp, 1, st)) != cudaSuccess) return e;
+  if ((e = raw_product(h, p, Kp, high, st)) != cudaSuccess) return e;
   high_op_kernel<<<grid_for(h->n), 256, 0, st>>>(Ap, Kp, p, L, sump, gam, h->n);
   h->launches++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -83,7 +91,10 @@ static cudaError_t high_operator(Handle* h, const double* p, double* Ap, double*
 enum CgState { CG_RUN = 0, CG_MET = 1, CG_TRUNC = 2, CG_NONFINITE = 3, CG_MAXIT = 4 };
 
 // a = rz / pAp, or the truncation step, into S_A; the pending status into S_PEND.
-__global__ void cg_alpha_kernel(double* __restrict__ s) {
+// noise_coef: the Gram product's rounding level in p^T A p per unit ||p||^2
+// (2^-22 sqrt(n) for FP32 entries and sums, far smaller for the FP64-class
+// product); a curvature below four times that level is rounding, not K.
+__global__ void cg_alpha_kernel(double* __restrict__ s, double noise_coef) {
   if ((int)s[S_CGST] != CG_RUN) {
     s[S_A] = 0.0;
     s[S_PEND] = s[S_CGST];
@@ -93,10 +104,11 @@ __global__ void cg_alpha_kernel(double* __restrict__ s) {
   if (!isfinite(pAp)) {
     s[S_A] = 0.0;
     s[S_PEND] = CG_NONFINITE;
-  } else if (!(pAp > 0.0)) {
-    // The operator is positive definite; a non-positive curvature is FP32 rounding in
-    // directions whose eigenvalues lie below the product's accuracy (a numerically
-    // low-rank K).  Truncate: keep x, or at the first step take the preconditioned
+  } else if (!(pAp > 4.0 * noise_coef * s[S_PP])) {
+    // The operator is positive definite; a curvature at or below the product's
+    // rounding level is rounding in directions whose eigenvalues lie below its
+    // accuracy (a numerically low-rank K), and dividing by it would blow the
+    // step up.  Truncate: keep x, or at the first step take the preconditioned
     // residual itself (a Newton step with the preconditioner as the Hessian model).
     s[S_A] = s[S_CGITS] == 0.0 ? 1.0 : 0.0;
     s[S_PEND] = CG_TRUNC;
@@ -140,6 +152,7 @@ __global__ void cg_init_kernel(double* __restrict__ s, double tol2, double maxit
 // CG iterations per host status read: one per product when a product costs far more
 // than a host round trip, more when the products are cheap (small n).
 static int cg_block(Handle* h) {
+  if (h->rdv) return 1;                 // grid columns meet at every product on the host
   if (h->n <= 8192) return 16;
   if (h->n <= 32768) return 4;
   return 1;
@@ -171,6 +184,9 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
   CK(reduce(h, RED_NORM2, rn, n, s + S_RR, st));
   CK(precond_apply(h, Lpre, r, zz, s + S_RZ, st));
   CK(vec_copy(h, p, zz, n, st));
+  RedArgs rp;
+  rp.a = p;
+  CK(reduce(h, RED_NORM2, rp, n, s + S_PP, st));
   cg_init_kernel<<<1, 1, 0, st>>>(s, tol * tol, (double)maxit, gam);
   h->launches++;
   CK(cudaGetLastError());
@@ -183,6 +199,11 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
     return KQR_OK;
   }
   const int block = cg_block(h);
+  const bool high_products = (h->rdv || !lowprec) && h->cg_high_on;
+  // TF32 CG (lowprec) is refined against FP32 residuals, which absorb its inaccuracy:
+  // there the guard only keeps the step from overflowing on a near-zero curvature.
+  const double noise_coef = std::sqrt((double)n) * (high_products ? std::ldexp(1.0, -44)
+                                                                   : (lowprec ? std::ldexp(1.0, -40) : std::ldexp(1.0, -22)));
   // One block of CG iterations, every scalar on the device.
   auto enqueue_block = [&]() -> cudaError_t {
     cudaError_t e = cudaSuccess;
@@ -195,11 +216,12 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
       ep.pvec = p;
       ep.dot_out = s + S_PAP;
       ep.raw_out = Kp;
-      if (h->cg_high_on && !lowprec) e = high_operator(h, p, Ap, Kp, L, gam, s + S_SUMP, s + S_PAP, st);
+      if (h->rdv) e = op_product(h, p, Ap, Kp, L, gam, s + S_SUMP, s + S_PAP, h->cg_high_on, st);
+      else if (h->cg_high_on && !lowprec) e = op_product(h, p, Ap, Kp, L, gam, s + S_SUMP, s + S_PAP, true, st);
       else if (lowprec) e = gram_rbf_tc(h, p, Ap, 1, false, &ep, st);
       else e = gram_f32(h, p, Ap, 1, &ep, st);
       if (e != cudaSuccess) break;
-      cg_alpha_kernel<<<1, 1, 0, st>>>(s);
+      cg_alpha_kernel<<<1, 1, 0, st>>>(s, noise_coef);
       h->launches++;
       if ((e = cudaGetLastError()) != cudaSuccess) break;
       if ((e = cg_update(h, x, Kx, r, p, Kp, Ap, s + S_A, n, s + S_RR, st)) != cudaSuccess) break;
@@ -210,7 +232,7 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
       cg_beta_kernel<<<1, 1, 0, st>>>(s);
       h->launches++;
       if ((e = cudaGetLastError()) != cudaSuccess) break;
-      e = cg_direction(h, p, zz, s + S_BETA, s + S_CGST, n, st);
+      e = cg_direction(h, p, zz, s + S_BETA, s + S_CGST, n, s + S_PP, st);
     }
     return e;
   };
@@ -219,7 +241,7 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
   // gam is read from S_GAM).  A graph is captured only after a block has run
   // directly with the same buffers, so that every buffer the products use exists
   // before capture; later calls with the same buffers launch it from the start.
-  const bool graphs = block > 1 && !h->profile && !h->cg_graphs_off && !(h->cg_high_on && !lowprec);
+  const bool graphs = block > 1 && !h->profile && !h->cg_graphs_off && !h->rdv && !(h->cg_high_on && !lowprec);
   Handle::CgGraph* g = nullptr;
   std::vector<const void*> key;
   if (graphs) {
@@ -380,6 +402,14 @@ static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// options.cg_high = 2: a CG run that stopped at a rounding-level curvature shows
+// that the FP32 products cannot resolve this operator (a numerically low-rank K);
+// the rest of the solve runs its CG products FP64-class.
+static void adapt_cg_products(Handle* h) {
+  if (h->opt.cg_high == 2 && !h->cg_high_on && h->cg_truncated && !(h->opt.cg_tf32 && h->kind == KQR_RBF))
+    h->cg_high_on = true;
+}
+
 kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) {
   const kqr_options& o = h->opt;
   const int64_t n = h->n;
@@ -438,8 +468,10 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
       KS(pcg_refined(h, L, Lpre, lam * sigma, b, alpha, Ka, k > 0, eps_k, o.pcg_maxit, &its, &inf.matvecs_fp32,
                      &inf.matvecs_low, st));
     } else {
+      const bool high_before = h->cg_high_on;
       KS(pcg(h, L, Lpre, lam * sigma, b, alpha, Ka, k > 0, eps_k, o.pcg_maxit, &its, st));
-      (h->cg_high_on ? inf.matvecs_high : inf.matvecs_fp32) += its;
+      (high_before ? inf.matvecs_high : inf.matvecs_fp32) += its;
+      adapt_cg_products(h);
     }
     inf.pcg_iters += its;
     RedArgs rs;
@@ -476,7 +508,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
   inf.phase1_iters = k;
 
   // FP64-class K alpha from here on.
-  CK(gram_high(h, alpha, Ka, 1, st));
+  CK(raw_product(h, alpha, Ka, true, st));
   inf.matvecs_high++;
   KS(kkt(h, alpha, v, beta, z, Ka, tau, lam, res, st));
   bool converged = std::fmax(res[3], res[4]) <= tol;
@@ -510,8 +542,10 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
           KS(pcg_refined(h, L, Lpre, lam * sigma, b, d, Kd, false, ptol, o.pcg_maxit, &its, &inf.matvecs_fp32,
                          &inf.matvecs_low, st));
         } else {
+          const bool high_before = h->cg_high_on;
           KS(pcg(h, L, Lpre, lam * sigma, b, d, Kd, false, ptol, o.pcg_maxit, &its, st));
-          (h->cg_high_on ? inf.matvecs_high : inf.matvecs_fp32) += its;
+          (high_before ? inf.matvecs_high : inf.matvecs_fp32) += its;
+          adapt_cg_products(h);
         }
         inf.pcg_iters += its;
         // Armijo backtracking on phi_k(alpha + c d) - phi_k(alpha), term by term.
@@ -535,7 +569,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
           c *= o.r_ls;
         }
         CK(axpy_vec(h, alpha, d, c, n, st));
-        CK(gram_high(h, alpha, Ka, 1, st));
+        CK(raw_product(h, alpha, Ka, true, st));
         inf.matvecs_high++;
         inf.newton_steps++;
         if (o.verbose)
@@ -588,6 +622,7 @@ kqr_status solve(Handle* h, double tau, double lam, double tol, kqr_info* info) 
   inf.core_builds = (int32_t)(h->core_builds - builds0);
   inf.cg_truncations = (int32_t)(h->cg_truncations - trunc0);
   inf.seconds = now_s() - t_start;
+  inf.cg_high_used = h->cg_high_on ? 1 : 0;
   if (info) *info = inf;
   if (status != KQR_OK) return status;
   if (o.phase1_only) return KQR_OK;

@@ -154,13 +154,20 @@ struct FCgUpdate {
   }
 };
 
-// p = z + beta p, unless the device-resident CG status (stop_dev, nullable) says it stopped.
-__global__ void cg_direction_kernel(double* p, const double* z, const double* beta_dev, const double* stop_dev,
-                                    int64_t n) {
-  if (stop_dev && *stop_dev != 0.0) return;
-  const double b = *beta_dev;
-  GRID_LOOP(i, n) p[i] = z[i] + b * p[i];
-}
+// p = z + beta p, unless the device-resident CG status (stop_dev, nullable) says it
+// stopped; and ||p||^2 of the resulting p.
+struct FCgDir {
+  double* p;
+  const double *z, *beta_dev, *stop_dev;
+  __device__ void operator()(int64_t i, double* acc) const {
+    double pi = p[i];
+    if (!(stop_dev && *stop_dev != 0.0)) {
+      pi = z[i] + (*beta_dev) * pi;
+      p[i] = pi;
+    }
+    acc[0] += pi * pi;
+  }
+};
 
 __global__ void op_residual_kernel(double* r, const double* b, const double* x, const double* Kx, double gam,
                                    const double* sum_x, const double* L, int64_t n) {
@@ -235,9 +242,8 @@ cudaError_t cg_update(Handle* h, double* x, double* Kx, double* r, const double*
   return run_reduce<1>(h, FCgUpdate{x, Kx, r, p, Kp, Ap, a_dev}, n, rr_out, st);
 }
 cudaError_t cg_direction(Handle* h, double* p, const double* z, const double* beta_dev, const double* stop_dev,
-                         int64_t n, cudaStream_t st) {
-  cg_direction_kernel<<<grid_for(n), 256, 0, st>>>(p, z, beta_dev, stop_dev, n);
-  return post(h);
+                         int64_t n, double* pp_out, cudaStream_t st) {
+  return run_reduce<1>(h, FCgDir{p, z, beta_dev, stop_dev}, n, pp_out, st);
 }
 cudaError_t op_residual(Handle* h, double* r, const double* b, const double* x, const double* Kx, double gam,
                         const double* sum_x, const double* L, int64_t n, cudaStream_t st) {

@@ -53,7 +53,7 @@ class Info(ctypes.Structure):
         ("eta_p", ctypes.c_double), ("eta_d", ctypes.c_double), ("eta_c", ctypes.c_double),
         ("eta_kkt", ctypes.c_double), ("eta_gap", ctypes.c_double), ("obj_p", ctypes.c_double),
         ("obj_d", ctypes.c_double), ("sigma_final", ctypes.c_double), ("seconds", ctypes.c_double),
-        ("gram_stored", ctypes.c_int32),
+        ("gram_stored", ctypes.c_int32), ("cg_high_used", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -72,6 +72,10 @@ SIGNATURES = {
     "kqr_create": (ctypes.c_int, [_DP, _DP, _I64, _I64, ctypes.c_int, _D, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
     "kqr_solve": (ctypes.c_int, [_P, _D, _D, _D, _DP, _DP, _DP, ctypes.POINTER(Info)]),
     "kqr_get_state": (ctypes.c_int, [_P, _DP, _DP]),
+    "kqr_solve_grid": (ctypes.c_int, [_P, _I64, _DP, _DP, _D, _DP, _DP, _DP, ctypes.POINTER(_I32),
+                                      ctypes.POINTER(Info)]),
+    "kqr_solve_grid_batch": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _DP, _DP, _D, _I32, _DP, _DP, _DP,
+                                            ctypes.POINTER(_I32)]),
     "kqr_kmatvec": (ctypes.c_int, [_P, _DP, _DP, _I64, ctypes.c_int]),
     "kqr_kmatvec_dev": (ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, _P]),
     "kqr_kmatvec_fp32_noalloc_dev": (ctypes.c_int, [_P, _P, _P, _I64, _P]),
@@ -218,6 +222,22 @@ class Problem:
         d = info.as_dict()
         d["status"] = st
         return alpha, beta.value, kkt.value, d
+
+    def solve_grid(self, taus, lambdas, tol: float = 1e-6):
+        """kqr_solve_grid: every (taus[c], lambdas[c]) pair on this problem.  Returns
+        alpha (n x m), beta (m), kkt (m), status (m) and the per-pair info dicts."""
+        taus = np.ascontiguousarray(taus, dtype=np.float64)
+        lambdas = np.ascontiguousarray(lambdas, dtype=np.float64)
+        m = taus.size
+        if lambdas.shape != taus.shape:
+            raise ValueError("taus and lambdas must have the same length")
+        alpha = np.empty((m, self.n))
+        beta, kkt = np.empty(m), np.empty(m)
+        status = np.empty(m, dtype=np.int32)
+        infos = (Info * m)()
+        self._check(self._lib.kqr_solve_grid(self._h, m, _dptr(taus), _dptr(lambdas), tol, _dptr(alpha), _dptr(beta),
+                                             _dptr(kkt), status.ctypes.data_as(ctypes.POINTER(_I32)), infos))
+        return alpha.T, beta, kkt, status, [i.as_dict() for i in infos]
 
     def state(self):
         v = np.empty(self.n)
@@ -452,3 +472,27 @@ def heldout_check_loss(X, y, Xh, yh, log_gamma, log_lambda, tau: float, tol: flo
             return (go * dX if ctx.want_dX else None), go * dg, go * dl
 
     return _HeldoutLoss.apply(X, log_gamma, log_lambda)
+
+
+def solve_grid_batch(problems, taus, lambdas, tol: float = 1e-6, workers: int = 4):
+    """kqr_solve_grid_batch over Problem objects with the same (tau, lambda)
+    pairs.  Returns per problem (alpha n_b x m, beta m, kkt m, status m)."""
+    taus = np.ascontiguousarray(taus, dtype=np.float64)
+    lambdas = np.ascontiguousarray(lambdas, dtype=np.float64)
+    m, B = taus.size, len(problems)
+    sizes = [p.n for p in problems]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    alpha = np.empty(int(off[-1]) * m)
+    beta, kkt = np.empty((B, m)), np.empty((B, m))
+    status = np.empty((B, m), dtype=np.int32)
+    hs = (_P * B)(*[p._h.value for p in problems])
+    st = lib().kqr_solve_grid_batch(hs, B, m, _dptr(taus), _dptr(lambdas), tol, workers, _dptr(alpha),
+                                    _dptr(beta), _dptr(kkt), status.ctypes.data_as(ctypes.POINTER(_I32)))
+    if st != OK:
+        msgs = [lib().kqr_last_error(p._h).decode() for p in problems]
+        raise KQRError(st, "; ".join(x for x in msgs if x))
+    out = []
+    for b in range(B):
+        a = alpha[off[b] * m:off[b + 1] * m].reshape(m, sizes[b]).T
+        out.append((a, beta[b], kkt[b], status[b]))
+    return out

@@ -114,7 +114,8 @@ def test_autograd_wrapper_matches_entry_point(K_):
     ll = torch.tensor(np.log(lam), dtype=torch.float64, requires_grad=True)
     out = K_.heldout_check_loss(Xt, tr.y, Xh, yh, lg, ll, tau, tol=1e-8)
     (2.0 * out).backward()
-    assert float(out.detach()) == pytest.approx(loss, rel=1e-9)
+    # two independent solves to KKT 1e-8 (the FP32 products accumulate in no fixed order)
+    assert float(out.detach()) == pytest.approx(loss, rel=1e-7)
     assert float(lg.grad) == pytest.approx(2 * dg, rel=1e-3, abs=1e-6)
     assert float(ll.grad) == pytest.approx(2 * dl, rel=1e-3, abs=1e-6)
     assert np.abs(Xt.grad.numpy() - 2 * dX).max() <= 1e-3 * (1 + np.abs(dX).max())
