@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--workload", default="lap_large")
     ap.add_argument("--n", type=int, default=0, help="override n (testing only)")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--tau", type=float, default=0.0, help="override the workload's tau")
     ap.add_argument("--rank0", type=int, default=1024, help="initial RPCholesky rank (library default: ceil(sqrt n))")
     ap.add_argument("--gram-store", type=int, default=0,
                     help="CG products from a stored K: 0 on the fly (the headline workload's stated form), "
@@ -77,6 +78,8 @@ def parse():
     ap.add_argument("--grid-nmax", type=int, default=20000, help="--mode grid: n_b ~ U{1000..nmax}")
     ap.add_argument("--grid-side", type=int, default=8, help="--mode grid: taus x lambdas = side x side pairs")
     ap.add_argument("--grid-workers", type=int, default=4, help="--mode grid: problems solved at a time")
+    ap.add_argument("--grid-lmin", type=float, default=1e-5, help="--mode grid: smallest lambda of the grid")
+    ap.add_argument("--grid-nl", type=int, default=0, help="--mode grid: number of lambdas (0: --grid-side)")
     ap.add_argument("--grid-seq-sample", type=int, default=32,
                     help="--mode grid: pairs solved one at a time through kqr_solve for the comparison")
     return ap.parse_args()
@@ -86,7 +89,8 @@ def workload(args, seed=0):
     from paper_2510_07929_gb300 import workloads as W
 
     gen = W.GENERATORS[args.workload]
-    return gen(n=args.n, seed=seed) if args.n else gen(seed=seed)
+    kw = {"tau": args.tau} if getattr(args, "tau", 0.0) else {}
+    return gen(n=args.n, seed=seed, **kw) if args.n else gen(seed=seed, **kw)
 
 
 def describe(wl, args):
@@ -699,16 +703,17 @@ def run_batch(args):
     return 0
 
 
-def grid_workload(problems: int, nmax: int, side: int, seed: int = 0):
+def grid_workload(problems: int, nmax: int, side: int, seed: int = 0, lmin: float = 1e-5, nl: int = 0):
     """The batched workload: problems with n_b ~ U{1000..nmax} (seed 0), each the
     rbf_small recipe at p = 8 from seed 1000 + b (x ~ U[0,1]^8, RBF gamma = 1/8),
-    and side taus in [0.05, 0.95] x side lambdas log-spaced in [1e-5, 1e-1]."""
+    and side taus in [0.05, 0.95] x (nl or side) lambdas log-spaced in [lmin, 1e-1]."""
     from paper_2510_07929_gb300 import workloads as W
 
     rng = np.random.default_rng(seed)
     sizes = rng.integers(1000, nmax + 1, size=problems)
     wls = [W.rbf_small(n=int(n), p=8, seed=1000 + b) for b, n in enumerate(sizes)]
-    taus, lams = np.meshgrid(np.linspace(0.05, 0.95, side), np.logspace(-5, -1, side), indexing="ij")
+    taus, lams = np.meshgrid(np.linspace(0.05, 0.95, side), np.logspace(np.log10(lmin), -1, nl or side),
+                             indexing="ij")
     return wls, taus.ravel(), lams.ravel()
 
 
@@ -727,7 +732,8 @@ def run_grid(args):
     build.build()
     from paper_2510_07929_gb300 import kqr
 
-    wls, taus, lams = grid_workload(args.grid_problems, args.grid_nmax, args.grid_side)
+    wls, taus, lams = grid_workload(args.grid_problems, args.grid_nmax, args.grid_side, lmin=args.grid_lmin,
+                                    nl=args.grid_nl)
     tol = args.tol
     t0 = time.perf_counter()
     probs = [kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, cg_high=2, time_limit_s=args.time_limit) for wl in wls]
@@ -747,22 +753,29 @@ def run_grid(args):
         sample = [(b, c) for b in range(len(wls)) for c in range(taus.size)]
     else:
         sample = sample[:args.grid_seq_sample]
-    seq = []
+    seq, seq_status = [], []
     for b, c in sample:
         t1 = time.perf_counter()
         _, _, kkt, info = probs[b].solve(float(taus[c]), float(lams[c]), tol, allow_not_converged=True)
         seq.append(time.perf_counter() - t1)
+        seq_status.append(int(info["status"]))
+    grid_sample_status = [int(out[b][3][c]) for b, c in sample]
     t_seq = sum(seq) if full else float(np.mean(seq)) * pairs
     for p in probs:
         p.close()
     res = {"mode": "grid",
            "workload": f"{len(wls)} RBF problems, n_b ~ U{{1000..{args.grid_nmax}}} (seed 0), p=8, gamma=1/8, "
-                       f"{args.grid_side} taus in [0.05, 0.95] x {args.grid_side} lambdas in [1e-5, 1e-1], tol {tol:g}",
+                       f"{args.grid_side} taus in [0.05, 0.95] x {args.grid_nl or args.grid_side} lambdas log-spaced in "
+                       f"[{args.grid_lmin:g}, 1e-1], tol {tol:g}",
            "sum_n": int(sum(w.n for w in wls)), "pairs": pairs, "create_s": t_create, "grid_s": t_grid,
            "grid_status_counts": {str(k): int(v) for k, v in zip(*np.unique(statuses, return_counts=True))},
            "grid_worst_kkt": worst,
            "sequential": {"kind": "measured" if full else "projection", "pairs_timed": len(seq),
-                          "seconds": t_seq, "mean_s_per_pair": float(np.mean(seq))},
+                          "seconds": t_seq, "mean_s_per_pair": float(np.mean(seq)),
+                          "status_counts": {str(k): int(v) for k, v in zip(*np.unique(seq_status, return_counts=True))},
+                          "grid_status_counts_same_pairs": {str(k): int(v) for k, v in
+                                                            zip(*np.unique(grid_sample_status, return_counts=True))}},
+           "time_limit_s_per_pair": args.time_limit,
            "speedup": t_seq / t_grid}
     print(json.dumps(res), flush=True)
     return 0

@@ -8,14 +8,18 @@
 // that shares the read-only state (the layouts of X, y, the RPCholesky factor
 // F, a stored K) and owns its mutable state (solver vectors, device scalars,
 // Woodbury core, stream).  Its Gram products go through a rendezvous: each
-// active column posts its vector and waits; the last one to arrive gathers all
-// posted vectors into n x m blocks of up to 8 columns, runs one multi-right-
+// active column posts its vector and waits; the leader gathers the posted
+// vectors into n x m blocks of up to 8 columns, runs one multi-right-
 // hand-side product per block on the base handle (FP32 and FP64-class requests
 // separately) and scatters the results, after which every column continues on
-// its own stream.  A column that has converged (or stopped) leaves the group,
-// so later products carry only the active columns.  Each column thread
-// synchronises with the others on the host at every product, so its CG runs
-// without CUDA graphs, one status read per iteration.
+// its own stream.  The first column to post leads: it waits a short window for
+// the others (all active columns, or whoever posted within 200 us) and runs the
+// batch, so a column that is busy elsewhere does not hold the rest back.  A
+// column that has converged (or stopped) leaves the group, so later products
+// carry only the active columns.  Each column thread meets the others on the
+// host at every product, so its CG runs without CUDA graphs, one status read
+// per iteration.
+#include <chrono>
 #include <condition_variable>
 #include <mutex>
 #include <thread>
@@ -30,21 +34,28 @@ struct GridRdv {
   cudaStream_t st = nullptr;
   std::mutex mu;
   std::condition_variable cv;
-  int active = 0;
-  uint64_t round = 0;
+  int active = 0;                 // columns still solving
+  bool leading = false;           // a column is gathering the next batch
   struct Req {
     const double* p;
     double* out;
     bool high;
     cudaEvent_t ready;
+    bool done;
   };
-  std::vector<Req> reqs;
-  cudaEvent_t done = nullptr;
+  std::vector<Req*> reqs;         // posted, not yet taken into a batch
+  cudaEvent_t done = nullptr;     // recorded after each batch (the product stream runs batches in order)
   cudaError_t err = cudaSuccess;
-  double* V = nullptr;     // gathered vectors, ldn x 8
-  double* U = nullptr;     // products, ldn x 8
+  double* V = nullptr;            // gathered vectors, ldn x 8
+  double* U = nullptr;            // products, ldn x 8
   int64_t rounds = 0, columns = 0;
 };
+
+// How long the first column to post a product waits for the others before it runs
+// the batch with whatever has been posted: long enough for columns that are between
+// two products of the same CG iteration, short enough that a column busy elsewhere
+// (a host read, a core build) does not hold the others back.
+constexpr auto kGridWindow = std::chrono::microseconds(200);
 
 struct Ptr8 {
   const double* p[8];
@@ -69,17 +80,17 @@ __global__ void grid_scatter_kernel(const double* __restrict__ U, int cnt, int64
   }
 }
 
-// Runs the posted products (caller holds the lock).
-static void run_round(GridRdv* g) {
+// Runs a batch of posted products (caller holds the lock).
+static void run_batch(GridRdv* g, std::vector<GridRdv::Req*>& batch) {
   Handle* b = g->base;
   cudaError_t e = cudaSuccess;
-  for (auto& r : g->reqs)
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->st, r.ready, 0);
+  for (auto* r : batch)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->st, r->ready, 0);
   for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
     const bool high = pass == 1;
     std::vector<GridRdv::Req*> sel;
-    for (auto& r : g->reqs)
-      if (r.high == high) sel.push_back(&r);
+    for (auto* r : batch)
+      if (r->high == high) sel.push_back(r);
     for (size_t k0 = 0; k0 < sel.size() && e == cudaSuccess; k0 += 8) {
       const int cnt = (int)std::min<size_t>(8, sel.size() - k0);
       Ptr8 src{};
@@ -110,30 +121,43 @@ static void run_round(GridRdv* g) {
   if (e == cudaSuccess) e = cudaEventRecord(g->done, g->st);
   if (e != cudaSuccess && g->err == cudaSuccess) g->err = e;
   g->rounds++;
-  g->reqs.clear();
-  g->round++;
-  g->cv.notify_all();
+  for (auto* r : batch) r->done = true;
 }
 
 cudaError_t grid_product(Handle* h, const double* p, double* out, bool high, cudaStream_t st) {
   GridRdv* g = h->rdv;
   cudaError_t e = cudaEventRecord(h->rdv_ev, st);
   if (e != cudaSuccess) return e;
+  GridRdv::Req me{p, out, high, h->rdv_ev, false};
   std::unique_lock<std::mutex> lk(g->mu);
-  g->reqs.push_back({p, out, high, h->rdv_ev});
-  const uint64_t mine = g->round;
-  if ((int)g->reqs.size() == g->active) run_round(g);
-  else g->cv.wait(lk, [&] { return g->round != mine; });
+  g->reqs.push_back(&me);
+  g->cv.notify_all();
+  while (!me.done) {
+    if (!g->leading) {
+      // lead: gather posts for up to kGridWindow (or until every active column posted)
+      g->leading = true;
+      g->cv.wait_for(lk, kGridWindow, [&] { return (int)g->reqs.size() >= g->active; });
+      std::vector<GridRdv::Req*> batch;
+      batch.swap(g->reqs);
+      run_batch(g, batch);
+      g->leading = false;
+      g->cv.notify_all();
+    } else {
+      g->cv.wait(lk);
+    }
+  }
   e = g->err;
   lk.unlock();
   if (e != cudaSuccess) return e;
+  // g->done holds this batch's record or a later one; the product stream runs batches
+  // in order, so either covers this column's product.
   return cudaStreamWaitEvent(st, g->done, 0);
 }
 
 static void grid_leave(GridRdv* g) {
   std::lock_guard<std::mutex> lk(g->mu);
   g->active--;
-  if (!g->reqs.empty() && (int)g->reqs.size() == g->active) run_round(g);
+  g->cv.notify_all();
 }
 
 // A column of the grid: the base handle's read-only state, its own mutable state.
