@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--path-tau", type=float, default=0.5)
     ap.add_argument("--path-lambdas", type=int, default=50)
     ap.add_argument("--path-precond", type=int, default=0, help="0 Nystrom+diag, 1 paper, 2 none (NALM)")
+    ap.add_argument("--path-kernel", default="rbf", choices=["rbf", "laplacian"])
     ap.add_argument("--path-first", type=int, nargs=2, default=None, metavar=("START", "STOP"),
                     help="--mode path: solve only lambdas[START:STOP] of the grid")
     ap.add_argument("--path-cg-high", type=int, default=2,
@@ -217,7 +218,7 @@ def job_throughput_value(total_ms: float, world: int, steps: int) -> float:
 def bench_config(wl, args, world: int) -> dict:
     """The bench line's config, shared by both arms."""
     return {"workload": describe(wl, args), "n": wl.n, "p": wl.p, "kernel": wl.kind, "rank0": args.rank0,
-            "xi": 1e-6, "preconditioner": "RPCholesky + floored residual diagonal (Woodbury)",
+            "xi": 1e-10, "preconditioner": "RPCholesky + floored residual diagonal (Woodbury)",
             "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1gpu"}
 
 
@@ -532,11 +533,21 @@ PAPER_TABLE1_S = {
 }
 
 
+# Total seconds of a 50-lambda path in the paper's Table 2 (Laplacian kernel, gamma = 0.1,
+# same generator, machine and tolerance as Table 1), keyed by (n, tau).  Context only.
+PAPER_TABLE2_S = {
+    (5000, 0.1): 139, (5000, 0.5): 143, (5000, 0.9): 141,
+    (10000, 0.1): 316, (10000, 0.5): 323, (10000, 0.9): 322,
+    (20000, 0.1): 1907, (20000, 0.5): 1899, (20000, 0.9): 1898,
+}
+
+
 def run_path(args):
     """A 50-lambda regularisation path (lambda log-spaced in [1e-2, 1]) on the
-    paper's p = 2 generator (Sec. 4.1), RBF kernel, tolerance 1e-8 per solve,
-    one handle (the RPCholesky factor is built once, as in Sec. 3), no warm
-    start across lambda."""
+    paper's p = 2 generator (Sec. 4.1), RBF or Laplacian kernel (--path-kernel),
+    tolerance 1e-8 per solve, one handle (the RPCholesky factor is built once,
+    as in Sec. 3), no warm start across lambda.  One JSON line per lambda, then
+    a summary line."""
     import torch
 
     from paper_2510_07929_gb300 import build, workloads as W
@@ -547,11 +558,13 @@ def run_path(args):
     n = args.n or 5000
     tol = 1e-8
     wl = W.yuan2006(n=n, gamma=args.path_gamma, tau=args.path_tau)
+    kind = args.path_kernel
     lams = np.logspace(-2, 0, args.path_lambdas)
     if args.path_first:
         lams = lams[args.path_first[0]:args.path_first[1]]
+    name = f"yuan2006 n={n} p=2 {kind} gamma={args.path_gamma:g} tau={args.path_tau:g}"
     t0 = time.perf_counter()
-    prob = kqr.Problem(wl.X, wl.y, wl.kind, wl.gamma, precond=args.path_precond, time_limit_s=args.time_limit,
+    prob = kqr.Problem(wl.X, wl.y, kind, wl.gamma, precond=args.path_precond, time_limit_s=args.time_limit,
                        cg_high=args.path_cg_high)
     t_setup = time.perf_counter() - t0
     per, worst, unsolved, products = [], 0.0, 0, 0
@@ -563,18 +576,23 @@ def run_path(args):
         worst = max(worst, max(kkt, info["eta_gap"]))
         unsolved += int(info["status"] != kqr.OK)
         products += info["matvecs_fp32"] + info["matvecs_high"]
-        print(f"lambda={lam:.4g} status={info['status']} kkt={kkt:.2e} gap={info['eta_gap']:.2e} s={per[-1]:.2f} "
-              f"cg={info['pcg_iters']} newton={info['newton_steps']} trunc={info['cg_truncations']}",
-              file=sys.stderr, flush=True)
+        print(json.dumps({"mode": "path_lambda", "workload": name, "lambda": float(lam), "status": info["status"],
+                          "kkt": kkt, "eta_gap": info["eta_gap"], "seconds": per[-1], "cg_iters": info["pcg_iters"],
+                          "newton_steps": info["newton_steps"], "alm_iters": info["phase2_iters"],
+                          "cg_truncations": info["cg_truncations"], "gram_fp32": info["matvecs_fp32"],
+                          "gram_high": info["matvecs_high"], "cg_high_used": info["cg_high_used"],
+                          "rank": info["rank"]}), flush=True)
     prob.close()
     total = t_setup + sum(per)
-    key = (n, args.path_gamma, args.path_tau)
-    out = {"mode": "path", "workload": f"yuan2006 n={n} p=2 rbf gamma={args.path_gamma:g} tau={args.path_tau:g}",
+    paper = (PAPER_TABLE1_S.get((n, args.path_gamma, args.path_tau)) if kind == "rbf"
+             else PAPER_TABLE2_S.get((n, args.path_tau)) if args.path_gamma == 0.1 else None)
+    out = {"mode": "path", "workload": name,
            "lambdas": len(lams), "tol": tol, "precond": ["nystrom_diag", "paper", "none"][args.path_precond],
            "cg_products": ["fp32", "fp64-class", "auto"][args.path_cg_high],
            "total_s": total, "setup_s": t_setup, "median_solve_s": float(np.median(per)), "max_solve_s": max(per),
            "worst_kkt_or_gap": worst, "not_converged": unsolved, "gram_products": products,
-           "paper_total_s": PAPER_TABLE1_S.get(key), "paper_hardware": "MATLAB, Xeon Platinum 8375C, 128 cores"}
+           "time_limit_s_per_lambda": args.time_limit,
+           "paper_total_s": paper, "paper_hardware": "MATLAB, Xeon Platinum 8375C, 128 cores (tables 1-2)"}
     print(json.dumps(out), flush=True)
     return 0
 

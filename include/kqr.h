@@ -102,7 +102,7 @@ typedef struct kqr_options {
   /* preconditioner set-up (Sec. 3) */
   int32_t rank0;                 /* initial RPCholesky rank r0; 0 = ceil(sqrt(n)) */
   int32_t adaptive_rank;         /* 1: pick r from the spectrum of F0^T F0 (Sec. 3); 0: r = r0 */
-  double xi;                     /* rank threshold: smallest r with xi * lambda_1 >= lambda_r (default 1e-6) */
+  double xi;                     /* rank threshold: smallest r with xi * lambda_1 >= lambda_r (default 1e-10) */
   uint64_t seed;                 /* pivot stream seed used when pivot_uniforms is NULL */
   const double* pivot_uniforms;  /* host, optional: one uniform [0,1) per pivot step, length >= r0 */
   kqr_precond precond;

@@ -349,7 +349,7 @@ void kqr_default_options(kqr_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->rank0 = 0;
   o->adaptive_rank = 1;
-  o->xi = 1e-6;
+  o->xi = 1e-10;
   o->seed = 12345;
   o->pivot_uniforms = nullptr;
   o->precond = KQR_PRECOND_NYSTROM_DIAG;

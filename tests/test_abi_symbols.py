@@ -60,7 +60,7 @@ def test_options_struct_layout_matches_c(lib_path):
     from paper_2510_07929_gb300 import kqr
 
     o = kqr.default_options()
-    assert o.xi == 1e-6 and o.seed == 12345 and o.gamma_admm == 1.618 and o.sigma_factor == 10.0
+    assert o.xi == 1e-10 and o.seed == 12345 and o.gamma_admm == 1.618 and o.sigma_factor == 10.0
     assert o.tau1 == 1e-2 and o.tau2 == 1e-1 and o.pcg_maxit == 1000 and o.verbose == 0 and o.sigma_alm_scale == 1.0
     assert o.core_reuse_rtol == 1e-2 and o.symmetric_gram == 1 and o.rbf_tensor_cores == 1 and o.cg_tf32 == 0
     assert o.cg_high == 2 and o.gram_store == 2
