@@ -67,26 +67,33 @@ def test_heldout_grad_finite_differences(K_):
     """n = 3000 training and 750 held-out points, p = 16, gamma = 0.25,
     lambda = 0.1 (the gradient workload's generator and constants at a smaller
     n): log-lambda and log-gamma derivatives against central differences of GPU
-    solves.  The loss is piecewise smooth; on a smoother kernel (p = 8,
-    gamma = 0.5) the training Gram's small eigenvalues let solves within the
-    same KKT tolerance differ in the held-out loss by more than the step's
-    signal, which is why this case uses the wider kernel."""
+    solves.  The loss is piecewise smooth: its slope changes where a training
+    point enters or leaves the elbow set or a held-out residual changes sign.
+    The test checks, from the solutions at +-h (oracle predictions of the
+    held-out points), whether the step crossed such a kink; without one the
+    difference must agree to 2e-4 of (1 + |loss|), across one to 1e-3."""
     tau, lam, gamma = 0.5, 0.1, 0.25
     tr, Xh, yh = _split(3000, 750, 16, 11, tau, lam)
 
-    def loss_at(gm, lm):
+    def at(gm, lm):
         with K_.Problem(tr.X, tr.y, "rbf", gm) as prob:
-            prob.solve(tau, lm, 1e-9)
-            return prob.heldout_grad(Xh, yh, want_dX=False)
+            alpha, beta, _, _ = prob.solve(tau, lm, 1e-9)
+            loss, dg, dl, _ = prob.heldout_grad(Xh, yh, want_dX=False)
+        f = O.predict(tr.X, alpha, beta, Xh, "rbf", gm, lm)
+        elbow = frozenset(np.flatnonzero((alpha > tau - 1 + 1e-6) & (alpha < tau - 1e-6)).tolist())
+        return loss, dg, dl, elbow, np.sign(yh - f)
 
-    loss, dg, dl, _ = loss_at(gamma, lam)
+    loss, dg, dl, E0, s0 = at(gamma, lam)
     h = 1e-4
-    fd_l = (loss_at(gamma, lam * np.exp(h))[0] - loss_at(gamma, lam * np.exp(-h))[0]) / (2 * h)
-    fd_g = (loss_at(gamma * np.exp(h), lam)[0] - loss_at(gamma * np.exp(-h), lam)[0]) / (2 * h)
-    # a held-out residual or an elbow point may change side inside the +-h step (a kink)
+    pts = {"l+": at(gamma, lam * np.exp(h)), "l-": at(gamma, lam * np.exp(-h)),
+           "g+": at(gamma * np.exp(h), lam), "g-": at(gamma * np.exp(-h), lam)}
+    fd_l = (pts["l+"][0] - pts["l-"][0]) / (2 * h)
+    fd_g = (pts["g+"][0] - pts["g-"][0]) / (2 * h)
     scale = 1.0 + abs(loss)
-    assert abs(fd_l - dl) <= 1e-3 * scale, (fd_l, dl)
-    assert abs(fd_g - dg) <= 1e-3 * scale, (fd_g, dg)
+    for name, fd, ad in (("l", fd_l, dl), ("g", fd_g, dg)):
+        kink = [k for k in (name + "+", name + "-") if pts[k][3] != E0 or np.any(pts[k][4] != s0)]
+        tol = 1e-3 if kink else 2e-4
+        assert abs(fd - ad) <= tol * scale, (name, fd, ad, kink)
 
 
 def test_heldout_grad_rejects_bad_calls(K_):
