@@ -16,9 +16,13 @@
 // the others (all active columns, or whoever posted within 200 us) and runs the
 // batch, so a column that is busy elsewhere does not hold the rest back.  A
 // column that has converged (or stopped) leaves the group, so later products
-// carry only the active columns.  Each column thread meets the others on the
-// host at every product, so its CG runs without CUDA graphs, one status read
-// per iteration.
+// carry only the active columns.  A column's CG (the bulk of the products)
+// runs in a shared engine instead: the column queues its CG set-up on its own
+// stream and posts the solve; a leader runs blocks of iterations for every
+// posted column (the products of all their directions on the base stream,
+// then each column's iteration chain on its own stream, forked and joined by
+// events) with one status read per block for all of them, and releases the
+// columns whose CG stopped.
 #include <chrono>
 #include <condition_variable>
 #include <mutex>
@@ -49,7 +53,21 @@ struct GridRdv {
   double* V = nullptr;            // gathered vectors, ldn x 8
   double* U = nullptr;            // products, ldn x 8
   int64_t rounds = 0, columns = 0;
+  // shared CG engine: columns waiting to join, columns iterating, the thread running blocks
+  struct CgJob {
+    Handle* h;
+    CgArgs a;
+    bool done;
+  };
+  std::vector<CgJob*> cg_new, cg_active;
+  bool cg_leading = false;
+  cudaEvent_t ev_scatter = nullptr, ev_block = nullptr;
+  double* status_host = nullptr;  // pinned, 2 per column (status, iterations)
+  int64_t cg_blocks = 0, cg_iterations = 0;
 };
+
+// CG iterations the engine runs between two status reads of its columns.
+constexpr int kGridCgBlock = 2;
 
 // How long the first column to post a product waits for the others before it runs
 // the batch with whatever has been posted: long enough for columns that are between
@@ -80,17 +98,22 @@ __global__ void grid_scatter_kernel(const double* __restrict__ U, int cnt, int64
   }
 }
 
-// Runs a batch of posted products (caller holds the lock).
-static void run_batch(GridRdv* g, std::vector<GridRdv::Req*>& batch) {
+// K p for each (p, out, high) on the base handle's stream, up to 8 columns per launch,
+// FP32 and FP64-class requests separately (caller holds the lock).
+struct ProdReq {
+  const double* p;
+  double* out;
+  bool high;
+};
+
+static cudaError_t run_products(GridRdv* g, const std::vector<ProdReq>& reqs) {
   Handle* b = g->base;
   cudaError_t e = cudaSuccess;
-  for (auto* r : batch)
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->st, r->ready, 0);
   for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
     const bool high = pass == 1;
-    std::vector<GridRdv::Req*> sel;
-    for (auto* r : batch)
-      if (r->high == high) sel.push_back(r);
+    std::vector<const ProdReq*> sel;
+    for (auto& r : reqs)
+      if (r.high == high) sel.push_back(&r);
     for (size_t k0 = 0; k0 < sel.size() && e == cudaSuccess; k0 += 8) {
       const int cnt = (int)std::min<size_t>(8, sel.size() - k0);
       Ptr8 src{};
@@ -118,10 +141,93 @@ static void run_batch(GridRdv* g, std::vector<GridRdv::Req*>& batch) {
       g->columns += cnt;
     }
   }
+  return e;
+}
+
+// Runs a batch of posted products (caller holds the lock).
+static void run_batch(GridRdv* g, std::vector<GridRdv::Req*>& batch) {
+  cudaError_t e = cudaSuccess;
+  for (auto* r : batch)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->st, r->ready, 0);
+  std::vector<ProdReq> reqs;
+  for (auto* r : batch) reqs.push_back({r->p, r->out, r->high});
+  if (e == cudaSuccess) e = run_products(g, reqs);
   if (e == cudaSuccess) e = cudaEventRecord(g->done, g->st);
   if (e != cudaSuccess && g->err == cudaSuccess) g->err = e;
   g->rounds++;
   for (auto* r : batch) r->done = true;
+}
+
+// One block of the shared CG engine (caller holds the lock; it is released while the
+// block runs on the GPU).  New columns join; every active column gets kGridCgBlock
+// iterations: per iteration, the products of all columns' search directions on the base
+// stream, then each column's chain (cg_after_product) on its own stream, the streams
+// forked and joined by events so the chains run side by side; then one status read for
+// all columns, after which the ones that stopped are released.
+static void run_cg_block(GridRdv* g, std::unique_lock<std::mutex>& lk) {
+  cudaError_t e = cudaSuccess;
+  for (auto* j : g->cg_new) {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->st, j->h->rdv_ev, 0);
+    g->cg_active.push_back(j);
+  }
+  g->cg_new.clear();
+  std::vector<GridRdv::CgJob*> act = g->cg_active;
+  if (act.empty()) return;
+  for (int it = 0; it < kGridCgBlock && e == cudaSuccess; ++it) {
+    std::vector<ProdReq> reqs;
+    for (auto* j : act) reqs.push_back({vec(j->h, V_P), vec(j->h, V_KP), j->h->cg_high_on});
+    if ((e = run_products(g, reqs)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(g->ev_scatter, g->st)) != cudaSuccess) break;
+    for (auto* j : act) {
+      cudaStream_t js = j->h->stream;
+      if ((e = cudaStreamWaitEvent(js, g->ev_scatter, 0)) != cudaSuccess) break;
+      if ((e = cg_after_product(j->h, j->a, js)) != cudaSuccess) break;
+      if ((e = cudaEventRecord(j->h->rdv_ev, js)) != cudaSuccess) break;
+      if ((e = cudaStreamWaitEvent(g->st, j->h->rdv_ev, 0)) != cudaSuccess) break;
+    }
+  }
+  for (size_t k = 0; k < act.size() && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(g->status_host + 2 * k, act[k]->h->scal + S_CGST, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                        g->st);
+  if (e == cudaSuccess) e = cudaEventRecord(g->ev_block, g->st);
+  lk.unlock();
+  if (e == cudaSuccess) e = cudaEventSynchronize(g->ev_block);
+  lk.lock();
+  g->cg_blocks++;
+  g->cg_iterations += (int64_t)kGridCgBlock * (int64_t)act.size();
+  if (e != cudaSuccess) {
+    if (g->err == cudaSuccess) g->err = e;
+    for (auto* j : act) j->done = true;   // the columns read the error and stop
+    g->cg_active.clear();
+    return;
+  }
+  std::vector<GridRdv::CgJob*> keep;
+  for (size_t k = 0; k < act.size(); ++k) {
+    if ((int)g->status_host[2 * k] != 0) act[k]->done = true;   // status left "running"
+    else keep.push_back(act[k]);
+  }
+  g->cg_active.swap(keep);
+}
+
+cudaError_t grid_cg(Handle* h, const CgArgs& a) {
+  GridRdv* g = h->rdv;
+  cudaError_t e = cudaEventRecord(h->rdv_ev, h->stream);   // the column's CG set-up is queued before this
+  if (e != cudaSuccess) return e;
+  GridRdv::CgJob me{h, a, false};
+  std::unique_lock<std::mutex> lk(g->mu);
+  g->cg_new.push_back(&me);
+  g->cv.notify_all();
+  while (!me.done) {
+    if (!g->cg_leading) {
+      g->cg_leading = true;
+      run_cg_block(g, lk);
+      g->cg_leading = false;
+      g->cv.notify_all();
+    } else {
+      g->cv.wait(lk);
+    }
+  }
+  return g->err;
 }
 
 cudaError_t grid_product(Handle* h, const double* p, double* out, bool high, cudaStream_t st) {
@@ -245,6 +351,10 @@ static kqr_status solve_grid(Handle* h, int64_t m, const double* taus, const dou
   std::vector<Handle*> cols(m, nullptr);
   kqr_status result = KQR_OK;
   if (!g.V || !g.U) result = fail(h, KQR_OOM, "grid product buffers");
+  if (result == KQR_OK && ((e = cudaEventCreateWithFlags(&g.ev_scatter, cudaEventDisableTiming)) != cudaSuccess ||
+                           (e = cudaEventCreateWithFlags(&g.ev_block, cudaEventDisableTiming)) != cudaSuccess ||
+                           (e = cudaMallocHost(&g.status_host, sizeof(double) * 2 * m)) != cudaSuccess))
+    result = cuda_fail(h, e, "grid CG engine");
   for (int64_t c = 0; c < m && result == KQR_OK; ++c) {
     kqr_status s = KQR_OK;
     cols[c] = column_clone(h, &g, &s);
@@ -290,6 +400,9 @@ static kqr_status solve_grid(Handle* h, int64_t m, const double* taus, const dou
   dev_free(h, g.V);
   dev_free(h, g.U);
   cudaEventDestroy(g.done);
+  if (g.ev_scatter) cudaEventDestroy(g.ev_scatter);
+  if (g.ev_block) cudaEventDestroy(g.ev_block);
+  if (g.status_host) cudaFreeHost(g.status_host);
   h->grid_rounds += g.rounds;
   h->grid_columns += g.columns;
   return result;

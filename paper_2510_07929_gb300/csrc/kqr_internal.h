@@ -256,6 +256,23 @@ kqr_status pcg_refined(Handle* h, const double* Ldiag, const double* Lpre, doubl
 kqr_status kkt(Handle* h, const double* alpha, const double* v, double beta, const double* z,
                const double* Kalpha, double tau, double lam, double* out7, cudaStream_t st);
 
+// One CG iteration after the Gram product K p has landed in vec(h, V_KP): the operator's
+// other terms, the device-resident step lengths and stopping test, the preconditioner and
+// the direction update (solver.cu).  Used by the grid's shared CG engine (grid.cu), which
+// runs the products of several columns together and this chain on each column's stream.
+struct CgArgs {
+  const double* L = nullptr;
+  const double* Lpre = nullptr;
+  double gam = 0.0;
+  double* x = nullptr;
+  double* Kx = nullptr;
+  double noise_coef = 0.0;
+};
+cudaError_t cg_after_product(Handle* h, const CgArgs& a, cudaStream_t st);
+// Runs a grid column's CG (set up by pcg on the column's stream) in the grid's shared
+// engine until its device status leaves "running" (grid.cu).
+cudaError_t grid_cg(Handle* h, const CgArgs& a);
+
 // Solver work vector slots in vec_pool.
 enum Vec {
   V_ALPHA = 0, V_V, V_Z, V_KALPHA, V_B, V_D, V_KD, V_R, V_ZZ, V_P, V_AP, V_KP, V_L, V_LPRE, V_GRAD,

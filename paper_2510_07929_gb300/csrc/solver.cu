@@ -158,6 +158,39 @@ static int cg_block(Handle* h) {
   return 1;
 }
 
+cudaError_t cg_after_product(Handle* h, const CgArgs& a, cudaStream_t st) {
+  const int64_t n = h->n;
+  double* s = h->scal;
+  double* r = vec(h, V_R);
+  double* zz = vec(h, V_ZZ);
+  double* p = vec(h, V_P);
+  double* Ap = vec(h, V_AP);
+  double* Kp = vec(h, V_KP);
+  RedArgs rs;
+  rs.a = p;
+  cudaError_t e = reduce(h, RED_SUM, rs, n, s + S_SUMP, st);
+  if (e != cudaSuccess) return e;
+  high_op_kernel<<<grid_for(n), 256, 0, st>>>(Ap, Kp, p, a.L, s + S_SUMP, a.gam, n);
+  h->launches++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  RedArgs rd;
+  rd.a = p;
+  rd.b = Ap;
+  if ((e = reduce(h, RED_DOT, rd, n, s + S_PAP, st)) != cudaSuccess) return e;
+  cg_alpha_kernel<<<1, 1, 0, st>>>(s, a.noise_coef);
+  h->launches++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cg_update(h, a.x, a.Kx, r, p, Kp, Ap, s + S_A, n, s + S_RR, st)) != cudaSuccess) return e;
+  cg_check_kernel<<<1, 1, 0, st>>>(s);
+  h->launches++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = precond_apply(h, a.Lpre, r, zz, s + S_RZN, st)) != cudaSuccess) return e;
+  cg_beta_kernel<<<1, 1, 0, st>>>(s);
+  h->launches++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cg_direction(h, p, zz, s + S_BETA, s + S_CGST, n, s + S_PP, st);
+}
+
 kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const double* b, double* x, double* Kx,
                bool warm, double tol, int maxit, int* iters, cudaStream_t st, bool lowprec) {
   const int64_t n = h->n;
@@ -252,6 +285,20 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
   }
   int state = CG_RUN, it = 0;
   bool first = true;
+  if (h->rdv) {
+    // a grid column: its iterations run in the grid's shared CG engine
+    CgArgs ca;
+    ca.L = L;
+    ca.Lpre = Lpre;
+    ca.gam = gam;
+    ca.x = x;
+    ca.Kx = Kx;
+    ca.noise_coef = noise_coef;
+    CK(grid_cg(h, ca));
+    CK(fetch(h, S_RR, S_CGITS - S_RR + 1, st));
+    state = (int)h->scal_host[S_CGST];
+    it = (int)h->scal_host[S_CGITS];
+  }
   while (state == CG_RUN) {
     if (graphs && !first && (!g->exec || g->key != key)) {
       // capture the block (relaxed mode: the launch helpers set kernel attributes)
