@@ -84,46 +84,87 @@ static cudaError_t op_product(Handle* h, const double* p, double* Ap, double* Kp
 }
 
 // ---- device-resident CG control ---------------------------------------------------
-// CG's scalars live in device slots; small single-thread kernels compute the step
-// lengths and the stopping test, so the host reads one status word per block of
-// iterations instead of three blocking copies per iteration.  Status (S_CGST):
+// CG's scalars live in device slots; the update and direction kernels compute the step
+// lengths and the stopping test themselves (in the CTA that finishes their reduction
+// last), so the host reads one status word per block of iterations instead of three
+// blocking copies per iteration.  Status (S_CGST):
 // 0 running, 1 met tol, 2 stopped at a non-positive curvature, 3 non-finite, 4 maxit.
 enum CgState { CG_RUN = 0, CG_MET = 1, CG_TRUNC = 2, CG_NONFINITE = 3, CG_MAXIT = 4 };
 
-// a = rz / pAp, or the truncation step, into S_A; the pending status into S_PEND.
-// noise_coef: the Gram product's rounding level in p^T A p per unit ||p||^2
-// (2^-22 sqrt(n) for FP32 entries and sums, far smaller for the FP64-class
-// product); a curvature below four times that level is rounding, not K.
-__global__ void cg_alpha_kernel(double* __restrict__ s, double noise_coef) {
-  if ((int)s[S_CGST] != CG_RUN) {
-    s[S_A] = 0.0;
-    s[S_PEND] = s[S_CGST];
-    return;
+// Block sum of v over the CTA's 256 threads into part[blockIdx.x]; returns true in the
+// CTA that finishes last, whose thread 0 then holds the sum over all CTAs (added in
+// CTA order) in *total.  Resets the counter for the next reduction.
+__device__ __forceinline__ bool cg_block_sum(double v, double* __restrict__ part, unsigned int* __restrict__ counter,
+                                             double* total) {
+  __shared__ double ws[8];
+  __shared__ bool last;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < 8; ++w) b += ws[w];
+    part[blockIdx.x] = b;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   }
+  __syncthreads();
+  if (!last) return false;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(part + b);
+    *total = t;
+    *counter = 0u;
+  }
+  return true;
+}
+
+// One CG step after p^T A p is known: the step length a = rz / pAp (rz in S_RZN), or the
+// truncation step when the curvature is at or below the product's rounding level
+// (noise_coef: that level per unit ||p||^2, 2^-22 sqrt(n) for FP32 entries and sums);
+// x += a p, Kx += a Kp, r -= a Ap; then, in the CTA that finishes last, ||r||^2, the
+// iteration count, rz copied to S_RZ for the next direction, and the status
+// (0 running, 1 met tol, 2 rounding-level curvature, 3 non-finite, 4 maxit).  A stopped CG
+// (status != 0, set by an earlier launch, so the same in every CTA) makes this a no-op.
+__global__ void __launch_bounds__(256) cg_step_kernel(double* __restrict__ s, double noise_coef, double* __restrict__ x,
+                                                      double* __restrict__ Kx, double* __restrict__ r,
+                                                      const double* __restrict__ p, const double* __restrict__ Kp,
+                                                      const double* __restrict__ Ap, int64_t n,
+                                                      double* __restrict__ part, unsigned int* __restrict__ counter) {
+  if ((int)s[S_CGST] != CG_RUN) return;
   const double pAp = s[S_PAP];
+  double a;
+  int pend;
   if (!isfinite(pAp)) {
-    s[S_A] = 0.0;
-    s[S_PEND] = CG_NONFINITE;
+    a = 0.0;
+    pend = CG_NONFINITE;
   } else if (!(pAp > 4.0 * noise_coef * s[S_PP])) {
     // The operator is positive definite; a curvature at or below the product's
     // rounding level is rounding in directions whose eigenvalues lie below its
-    // accuracy (a numerically low-rank K), and dividing by it would blow the
-    // step up.  Truncate: keep x, or at the first step take the preconditioned
-    // residual itself (a Newton step with the preconditioner as the Hessian model).
-    s[S_A] = s[S_CGITS] == 0.0 ? 1.0 : 0.0;
-    s[S_PEND] = CG_TRUNC;
+    // accuracy (a numerically low-rank K), and dividing by it would blow the step
+    // up.  Truncate: keep x, or at the first step take the preconditioned residual
+    // itself (a Newton step with the preconditioner as the Hessian model).
+    a = s[S_CGITS] == 0.0 ? 1.0 : 0.0;
+    pend = CG_TRUNC;
   } else {
-    s[S_A] = s[S_RZ] / pAp;
-    s[S_PEND] = CG_RUN;
+    a = s[S_RZN] / pAp;
+    pend = CG_RUN;
   }
-}
-
-// After the update: iteration count and stopping test.
-__global__ void cg_check_kernel(double* __restrict__ s) {
-  if ((int)s[S_CGST] != CG_RUN) return;
-  const int pend = (int)s[S_PEND];
-  if (s[S_A] != 0.0) s[S_CGITS] += 1.0;
-  const double rr = s[S_RR];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += a * p[i];
+    if (Kx) Kx[i] += a * Kp[i];
+    const double ri = r[i] - a * Ap[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double rr;
+  if (!cg_block_sum(acc, part, counter, &rr) || threadIdx.x != 0) return;
+  s[S_RR] = rr;
+  s[S_A] = a;
+  s[S_RZ] = s[S_RZN];
+  if (a != 0.0) s[S_CGITS] += 1.0;
   int st = pend;
   if (st == CG_RUN) {
     if (!isfinite(rr)) st = CG_NONFINITE;
@@ -133,12 +174,36 @@ __global__ void cg_check_kernel(double* __restrict__ s) {
   s[S_CGST] = st;
 }
 
-// beta = rz_new / rz and rz <- rz_new while running.
-__global__ void cg_beta_kernel(double* __restrict__ s) {
+// p = z + beta p with beta = rz_new / rz (S_RZN, S_RZ), and ||p||^2 into S_PP, while CG runs.
+__global__ void __launch_bounds__(256) cg_dir_kernel(double* __restrict__ s, double* __restrict__ p,
+                                                     const double* __restrict__ z, int64_t n,
+                                                     double* __restrict__ part, unsigned int* __restrict__ counter) {
   if ((int)s[S_CGST] != CG_RUN) return;
-  const double rzn = s[S_RZN];
-  s[S_BETA] = rzn / s[S_RZ];
-  s[S_RZ] = rzn;
+  const double b = s[S_RZN] / s[S_RZ];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double pi = z[i] + b * p[i];
+    p[i] = pi;
+    acc += pi * pi;
+  }
+  double pp;
+  if (!cg_block_sum(acc, part, counter, &pp) || threadIdx.x != 0) return;
+  s[S_PP] = pp;
+  s[S_BETA] = b;
+}
+
+static cudaError_t cg_step(Handle* h, double noise_coef, double* x, double* Kx, double* r, const double* p,
+                           const double* Kp, const double* Ap, cudaStream_t st) {
+  cg_step_kernel<<<grid_for(h->n, 256, 304), 256, 0, st>>>(h->scal, noise_coef, x, Kx, r, p, Kp, Ap, h->n, h->red_part,
+                                                           h->red_counter);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+static cudaError_t cg_dir(Handle* h, double* p, const double* z, cudaStream_t st) {
+  cg_dir_kernel<<<grid_for(h->n, 256, 304), 256, 0, st>>>(h->scal, p, z, h->n, h->red_part, h->red_counter);
+  h->launches++;
+  return cudaGetLastError();
 }
 
 __global__ void cg_init_kernel(double* __restrict__ s, double tol2, double maxit, double gam) {
@@ -177,18 +242,9 @@ cudaError_t cg_after_product(Handle* h, const CgArgs& a, cudaStream_t st) {
   rd.a = p;
   rd.b = Ap;
   if ((e = reduce(h, RED_DOT, rd, n, s + S_PAP, st)) != cudaSuccess) return e;
-  cg_alpha_kernel<<<1, 1, 0, st>>>(s, a.noise_coef);
-  h->launches++;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = cg_update(h, a.x, a.Kx, r, p, Kp, Ap, s + S_A, n, s + S_RR, st)) != cudaSuccess) return e;
-  cg_check_kernel<<<1, 1, 0, st>>>(s);
-  h->launches++;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cg_step(h, a.noise_coef, a.x, a.Kx, r, p, Kp, Ap, st)) != cudaSuccess) return e;
   if ((e = precond_apply(h, a.Lpre, r, zz, s + S_RZN, st)) != cudaSuccess) return e;
-  cg_beta_kernel<<<1, 1, 0, st>>>(s);
-  h->launches++;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return cg_direction(h, p, zz, s + S_BETA, s + S_CGST, n, s + S_PP, st);
+  return cg_dir(h, p, zz, st);
 }
 
 kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const double* b, double* x, double* Kx,
@@ -215,7 +271,7 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
   RedArgs rn;
   rn.a = r;
   CK(reduce(h, RED_NORM2, rn, n, s + S_RR, st));
-  CK(precond_apply(h, Lpre, r, zz, s + S_RZ, st));
+  CK(precond_apply(h, Lpre, r, zz, s + S_RZN, st));
   CK(vec_copy(h, p, zz, n, st));
   RedArgs rp;
   rp.a = p;
@@ -254,18 +310,9 @@ kqr_status pcg(Handle* h, const double* L, const double* Lpre, double gam, const
       else if (lowprec) e = gram_rbf_tc(h, p, Ap, 1, false, &ep, st);
       else e = gram_f32(h, p, Ap, 1, &ep, st);
       if (e != cudaSuccess) break;
-      cg_alpha_kernel<<<1, 1, 0, st>>>(s, noise_coef);
-      h->launches++;
-      if ((e = cudaGetLastError()) != cudaSuccess) break;
-      if ((e = cg_update(h, x, Kx, r, p, Kp, Ap, s + S_A, n, s + S_RR, st)) != cudaSuccess) break;
-      cg_check_kernel<<<1, 1, 0, st>>>(s);
-      h->launches++;
-      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      if ((e = cg_step(h, noise_coef, x, Kx, r, p, Kp, Ap, st)) != cudaSuccess) break;
       if ((e = precond_apply(h, Lpre, r, zz, s + S_RZN, st)) != cudaSuccess) break;
-      cg_beta_kernel<<<1, 1, 0, st>>>(s);
-      h->launches++;
-      if ((e = cudaGetLastError()) != cudaSuccess) break;
-      e = cg_direction(h, p, zz, s + S_BETA, s + S_CGST, n, s + S_PP, st);
+      e = cg_dir(h, p, zz, st);
     }
     return e;
   };
