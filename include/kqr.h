@@ -67,7 +67,9 @@ typedef enum kqr_kernel {
 /* Arithmetic of a Gram product.
  * KQR_PREC_HIGH: entries and sums accurate to about 1e-13 relative (FP64 class;
  *   Laplacian: exact fixed-point L1 distances plus double-float exp and sums on
- *   the FP32/INT32 pipes; RBF: FP64).  Used for gradients and KKT residuals.
+ *   the FP32/INT32 pipes; RBF with p <= 40: the same fixed-point scheme on the
+ *   squared differences; RBF with p > 40: FP64 arithmetic).  Used for gradients
+ *   and KKT residuals, and for CG where FP32 cannot resolve K (options.cg_high).
  * KQR_PREC_FP32: FP32 entries and FP32 partial sums, about 1e-6 relative per
  *   entry.  Used inside CG.  RBF: the cross term x_i . x_j runs on the tcgen05
  *   tensor cores as three TF32 products (hi.hi + hi.lo + lo.hi of a TF32 split
