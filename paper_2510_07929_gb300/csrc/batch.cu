@@ -77,10 +77,6 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_arrive_1(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
@@ -431,8 +427,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
         if (!PT) fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive_1(&s_empty[sb]);
-          mbar_arrive_1(&p_full[pb]);
+          mbar_arrive(&s_empty[sb]);
+          mbar_arrive(&p_full[pb]);
         }
       }
       if (!ok) break;
@@ -454,7 +450,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       }
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive_1(&u_empty[ub]);
+      if (lane == 0) mbar_arrive(&u_empty[ub]);
     }
   }
   fence_before();

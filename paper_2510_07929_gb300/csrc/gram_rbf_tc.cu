@@ -19,6 +19,7 @@
 // gridDim.y; per-split row sums are added in FP64 by a second kernel.
 // Every mbarrier wait is bounded; on a timeout the CTA records the error,
 // stops issuing work and frees its tensor memory.
+#include <algorithm>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -467,8 +468,313 @@ static cudaError_t rbf_tc_product(Handle* h, const double* V, double* U, int m, 
   return cudaGetLastError();
 }
 
+// ---- symmetric tiles for one right-hand side ------------------------------------------
+// K is symmetric, so each off-diagonal 128 x 128 tile K_JI (J > I) is formed once on the
+// tensor cores and used twice: u_J += K_JI v_I and u_I += K_JI^T v_J.  A work unit is a
+// row tile I and a run of column tiles J in [J0, J1) with J0 >= I.  The MMA computes
+// D = X_J X_I^T, so TMEM lane l is row j = J*128 + l and TMEM column c is i = I*128 + c.
+//
+// One CTA = 16 warps; warp w reads TMEM lanes 32 (w mod 4) .. + 31 (the lanes its warp
+// may access) over the 32 columns 32 (w / 4) .. + 31.  Per element a thread forms
+// e = exp2(2 xs_j.xs_i - n_j [- n_i]) and adds e w_i to its row j's sum (a register sum:
+// u_J needs no exchange between threads) and e v_j to column i's sum, which stays in a
+// register across all tiles of the unit (I is fixed), so the exchange across the warp's
+// 32 rows happens once per unit.  With FOLD (every n < 60) exp2(-n_i) is folded into
+// w_i = v_i exp2(-n_i) and exp2(-n_j) into the row and column results.
+//
+// No CTA-wide barrier inside the tile loop: thread 0 issues the TMA copies and MMAs; a
+// copy refills a stage once the MMAs that read it have completed (mma_done), an MMA
+// reuses a TMEM buffer once all 16 warps have read it out (tmem_free, one arrival per
+// warp).  Row sums go to the output with FP32 atomics per tile, column sums per unit.
+// Every wait is bounded; on a timeout the CTA records the error, drains its own copies
+// and MMAs (bounded) and frees its tensor memory.
+constexpr int kSymWarps = 8;
+constexpr int kSymCols = 64;  // columns of tile I per warp: two 32-column TMEM loads
+constexpr int kSymBufs = 2;   // TMEM accumulator buffers of 128 columns (two CTAs per SM)
+
+// nstage X_J stages; the MMAs of tile q are issued nstage / 2 iterations before its
+// epilogue, and the copy of tile q + nstage is issued as soon as the MMAs of tile q have
+// completed.
+template <int NTERMS, bool FOLD>
+__global__ void __launch_bounds__(kSymWarps * 32, 2)
+    gram_rbf_tc_sym_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+                           const float* __restrict__ nrm, const float* __restrict__ v32, const int4* __restrict__ units,
+                           float* __restrict__ acc, int ksteps, int katoms, int nstage, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  const uint32_t tb = (uint32_t)katoms * kAtomBytes;
+  unsigned char* XIh = base;
+  unsigned char* XIl = XIh + tb;
+  // stage s: hi part at base + (2 + 2 s) tb, lo part right after it
+  float* s_w = reinterpret_cast<float*>(base + (size_t)(2 + 2 * nstage) * tb);   // [128] column factors of tile I
+  float* s_ni = s_w + 128;                                                       // [128] n_i of tile I (without FOLD)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_ni + 128);
+  uint64_t* full_i = &bars[0];
+  uint64_t* full_j = &bars[1];                   // [nstage] X_J stage landed
+  uint64_t* mma_done = &bars[1 + 4];             // [kSymBufs] MMAs of TMEM buffer b completed
+  uint64_t* tmem_free = &bars[1 + 4 + kSymBufs]; // [kSymBufs] all warps have read TMEM buffer b
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + 4 + 2 * kSymBufs);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // thread 0's bookkeeping, in shared memory to spare registers: the latest tile whose copy,
+  // and the latest whose MMAs, may still be in flight
+  int* load_pending = reinterpret_cast<int*>(tmem_slot + 2);
+  int* mma_pending = load_pending + 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lq = warp & 3, cq = warp >> 2;
+  const int4 unit = units[blockIdx.x];
+  const int ti = unit.x;
+  const int jt0 = unit.y, jt1 = unit.z;
+  const int nt = jt1 - jt0;
+  const int look = nstage / 2;
+  const uint32_t load_bytes = (NTERMS == 3 ? 2u : 1u) * tb;
+
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 128 * kSymBufs);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(full_i, 1);
+    for (int s = 0; s < nstage; ++s) mbar_init(&full_j[s], 1);
+    for (int b = 0; b < kSymBufs; ++b) {
+      mbar_init(&mma_done[b], 1);
+      mbar_init(&tmem_free[b], kSymWarps);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (tid < 128) {
+    const float n_i = nrm[ti * 128 + tid];
+    s_w[tid] = v32[ti * 128 + tid] * (FOLD ? ex2_approx(-n_i) : 1.f);
+    s_ni[tid] = n_i;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto stage_hi = [&](int s) { return base + (size_t)(2 + 2 * s) * tb; };
+  auto load_tile = [&](int t) {   // tile t of the unit into stage t mod nstage
+    const int s = t % nstage;
+    unsigned char* dh = stage_hi(s);
+    mbar_arrive_expect_tx(&full_j[s], load_bytes);
+    for (int a = 0; a < katoms; ++a) {
+      tma_load_2d(dh + a * kAtomBytes, &tm_hi, a * 32, (jt0 + t) * 128, &full_j[s]);
+      if (NTERMS == 3) tma_load_2d(dh + tb + a * kAtomBytes, &tm_lo, a * 32, (jt0 + t) * 128, &full_j[s]);
+    }
+  };
+  if (tid == 0) {
+    *load_pending = -1;
+    *mma_pending = -1;
+    mbar_arrive_expect_tx(full_i, load_bytes);
+    for (int a = 0; a < katoms; ++a) {
+      tma_load_2d(XIh + a * kAtomBytes, &tm_hi, a * 32, ti * 128, full_i);
+      if (NTERMS == 3) tma_load_2d(XIl + a * kAtomBytes, &tm_lo, a * 32, ti * 128, full_i);
+    }
+    for (int t = 0; t < nstage && t < nt; ++t) {
+      load_tile(t);
+      *load_pending = t;
+    }
+  }
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  float cacc[kSymCols];   // column sums of tile I over this warp's 32 rows, across the unit's tiles
+#pragma unroll
+  for (int c = 0; c < kSymCols; ++c) cacc[c] = 0.f;
+  bool ok = true;   // warp-uniform: every wait of this warp succeeded
+  // this thread's row of the next epilogue tile, loaded one tile ahead
+  const int jrow = jt0 * 128 + lq * 32 + lane;
+  float n_nx = __ldg(nrm + jrow);
+  float v_nx = jt0 == ti ? 0.f : __ldg(v32 + jrow);   // the diagonal tile gives row sums only
+
+  for (int q = 0; q < nt + look; ++q) {
+    if (tid == 0 && q < nt) {
+      const int s = q % nstage, b = q % kSymBufs;
+      bool w_ok = true;
+      if (q == 0) w_ok = mbar_wait_bounded(full_i, 0, err);
+      if (w_ok) w_ok = mbar_wait_bounded(&full_j[s], (uint32_t)((q / nstage) & 1), err);
+      // TMEM buffer b last held tile q - kSymBufs: every warp must have read it out
+      if (w_ok && q >= kSymBufs)
+        w_ok = mbar_wait_bounded(&tmem_free[b], (uint32_t)((q / kSymBufs - 1) & 1), err);
+      if (w_ok) {
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * 128);
+        const unsigned char* ah = stage_hi(s);
+        const unsigned char* al = ah + tb;
+        for (int k = 0; k < ksteps; ++k) {
+          const uint32_t off = (uint32_t)(k >> 2) * kAtomBytes + (uint32_t)(k & 3) * 32u;
+          umma_tf32(d, umma_desc_sw128(ah + off), umma_desc_sw128(XIh + off), idesc, k > 0 ? 1u : 0u);
+          if (NTERMS == 3) {
+            umma_tf32(d, umma_desc_sw128(ah + off), umma_desc_sw128(XIl + off), idesc, 1u);
+            umma_tf32(d, umma_desc_sw128(al + off), umma_desc_sw128(XIh + off), idesc, 1u);
+          }
+        }
+        umma_commit(&mma_done[b]);
+        *mma_pending = q;
+      } else {
+        *abort_flag = 1;
+      }
+    }
+    if (q >= look) {
+      const int pq = q - look, b = pq % kSymBufs;
+      const float n_j = n_nx, v_j = v_nx;
+      if (pq + 1 < nt) {
+        n_nx = __ldg(nrm + jrow + (pq + 1) * 128);
+        v_nx = jt0 + pq + 1 == ti ? 0.f : __ldg(v32 + jrow + (pq + 1) * 128);
+      }
+      const bool landed = __all_sync(
+          0xffffffffu, *abort_flag == 0 && mbar_wait_bounded(&mma_done[b], (uint32_t)((pq / kSymBufs) & 1), err));
+      if (!landed) {
+        ok = false;
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      // the MMAs of tile pq have completed, so its stage is free: refill it with tile pq + nstage
+      if (tid == 0 && pq + nstage < nt) {
+        load_tile(pq + nstage);
+        *load_pending = pq + nstage;
+      }
+      float racc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int h = 0; h < kSymCols / 32; ++h) {
+      float g[32];
+      tmem_ld32(tmem + (uint32_t)(b * 128 + cq * kSymCols + h * 32) + ((uint32_t)(lq * 32) << 16), g);
+      if (h == kSymCols / 32 - 1) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tmem_free[b]);
+      }
+      const float* wq = s_w + cq * kSymCols + h * 32;
+      const float* nq = s_ni + cq * kSymCols + h * 32;
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {
+        const float4 w4 = *reinterpret_cast<const float4*>(wq + c4 * 4);
+        const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
+        float nn[4] = {n_j, n_j, n_j, n_j};
+        if (!FOLD) {
+          const float4 n4 = *reinterpret_cast<const float4*>(nq + c4 * 4);
+          nn[0] += n4.x;
+          nn[1] += n4.y;
+          nn[2] += n4.z;
+          nn[3] += n4.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c4 * 4 + u;
+          const float e = ex2_approx(fmaf(2.f, g[c], -nn[u]));
+          racc[u] = fmaf(e, ww[u], racc[u]);
+          cacc[h * 32 + c] = fmaf(e, v_j, cacc[h * 32 + c]);
+        }
+      }
+      }
+      atomicAdd(acc + jrow + pq * 128, (racc[0] + racc[1]) + (racc[2] + racc[3]));
+    }
+  }
+  // column sums: reduce-scatter each 32 column partials over the warp's 32 rows, so that
+  // lane l ends with column cq kSymCols + 32 h + l of tile I
+  if (__all_sync(0xffffffffu, ok && *abort_flag == 0)) {
+#pragma unroll
+    for (int h = 0; h < kSymCols / 32; ++h) {
+      float* ch = cacc + h * 32;
+#pragma unroll
+      for (int w = 16; w >= 1; w >>= 1) {
+        const bool up = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+          const float keep = up ? ch[i + w] : ch[i], send = up ? ch[i] : ch[i + w];
+          ch[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+      }
+      const int col = cq * kSymCols + h * 32 + lane;
+      const float f = FOLD ? ex2_approx(-s_ni[col]) : 1.f;
+      atomicAdd(acc + ti * 128 + col, ch[0] * f);
+    }
+  }
+  if (tid == 0 && *abort_flag) {
+    // a wait gave up: let this CTA's own copies and MMAs finish (bounded) before it frees
+    // its tensor memory and exits; copies go out in tile order, so each stage's latest is
+    // one of the last nstage tiles issued, and the last commit covers every earlier MMA
+    mbar_wait_bounded(full_i, 0, err);
+    const int lp = *load_pending, mp = *mma_pending;
+    for (int t = lp; t >= 0 && t > lp - nstage; --t)
+      mbar_wait_bounded(&full_j[t % nstage], (uint32_t)((t / nstage) & 1), err);
+    if (mp >= 0) mbar_wait_bounded(&mma_done[mp % kSymBufs], (uint32_t)((mp / kSymBufs) & 1), err);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128 * kSymBufs);
+}
+
+static int tc_sym_stages(int) { return 2; }
+
+static size_t tc_sym_smem(int katoms) {
+  return 1024 + (size_t)(2 + 2 * tc_sym_stages(katoms)) * katoms * kAtomBytes + 256 * sizeof(float) +
+         (1 + 4 + 2 * kSymBufs) * sizeof(uint64_t) + 32;
+}
+
+cudaError_t sym_prep(Handle* h, const double* V, float* v32, float* acc, double* sum_out, cudaStream_t st);
+
+// Work units of the symmetric tensor-core tiles: (row tile I, column tiles [J0, J1)) with
+// I <= J0, about 8 per SM (one CTA resident), so that each CTA's TMA/MMA pipeline runs over
+// tens of tiles; the longest units come first, for the block scheduler's tail.
+static cudaError_t tc_sym_units_ensure(Handle* h) {
+  const int T = (int)(h->ldn / kTile);
+  if (h->tc_sym_units && h->tc_sym_T == T) return cudaSuccess;
+  const int64_t pairs = (int64_t)T * (T + 1) / 2;
+  const int64_t target = (int64_t)8 * h->num_sms;
+  int C = (int)((pairs + target - 1) / target);
+  if (C < 1) C = 1;
+  std::vector<int4> u;
+  for (int I = 0; I < T; ++I)
+    for (int J0 = I; J0 < T; J0 += C) u.push_back(make_int4(I, J0, J0 + C < T ? J0 + C : T, 0));
+  std::stable_sort(u.begin(), u.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
+  dev_free(h, h->tc_sym_units);
+  h->tc_sym_units = (int4*)dev_alloc(h, u.size() * sizeof(int4));
+  if (!h->tc_sym_units) return cudaErrorMemoryAllocation;
+  h->tc_sym_nunits = (int)u.size();
+  h->tc_sym_T = T;
+  return cudaMemcpy(h->tc_sym_units, u.data(), u.size() * sizeof(int4), cudaMemcpyHostToDevice);
+}
+cudaError_t sym_finish(Handle* h, const float* acc, double* U, const GramEpilogue& g, cudaStream_t st);
+
+// m = 1 RBF product on symmetric tensor-core tiles; nt = 3: FP32 class, 1: TF32.
+static cudaError_t rbf_tc_sym_product(Handle* h, const double* V, double* U, int nt, const GramEpilogue* ep,
+                                      cudaStream_t st) {
+  cudaError_t e = rbf_tc_prepare(h);
+  if (e != cudaSuccess) return e;
+  if ((e = tc_sym_units_ensure(h)) != cudaSuccess) return e;
+  const size_t need = (size_t)h->ldn * sizeof(float) * 2;   // v32 + acc
+  if (h->v32_cap < need) {
+    dev_free(h, h->v32);
+    h->v32 = (float*)dev_alloc(h, need);
+    h->v32_cap = h->v32 ? need : 0;
+    if (!h->v32) return cudaErrorMemoryAllocation;
+  }
+  float* v32 = h->v32;
+  float* acc = h->v32 + h->ldn;
+  GramEpilogue none;
+  const GramEpilogue& g = ep ? *ep : none;
+  if ((e = sym_prep(h, V, v32, acc, g.sum_p ? const_cast<double*>(g.sum_p) : nullptr, st)) != cudaSuccess) return e;
+  const int katoms = h->tc_Kp / 32;
+  const int ksteps = (int)((h->p + 7) / 8);
+  const size_t smem = tc_sym_smem(katoms);
+  auto kern = nt == 3 ? (h->tc_fold_rows ? gram_rbf_tc_sym_kernel<3, true> : gram_rbf_tc_sym_kernel<3, false>)
+                      : (h->tc_fold_rows ? gram_rbf_tc_sym_kernel<1, true> : gram_rbf_tc_sym_kernel<1, false>);
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  prof_mark(h, 0, true, st);
+  kern<<<h->tc_sym_nunits, kSymWarps * 32, smem, st>>>(h->tm_tc_hi, h->tm_tc_lo, h->nrm32, v32, h->tc_sym_units, acc,
+                                                       ksteps, katoms, tc_sym_stages(katoms), h->err_flag);
+  prof_mark(h, 0, false, st);
+  h->launches++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return sym_finish(h, acc, U, g, st);
+}
+
 cudaError_t gram_rbf_tc(Handle* h, const double* V, double* U, int m, bool three_terms, const GramEpilogue* ep,
                         cudaStream_t st) {
+  if (m == 1 && h->opt.symmetric_gram) return rbf_tc_sym_product(h, V, U, three_terms ? 3 : 1, ep, st);
   return rbf_tc_product(h, V, U, m, three_terms ? 3 : 1, ep, st);
 }
 

@@ -128,6 +128,8 @@ struct Handle {
   // Symmetric Gram product: work-unit table (row tile, first and end column tile).
   int4* sym_units = nullptr;
   int sym_nunits = 0, sym_T = 0;
+  int4* tc_sym_units = nullptr;       // the same for the symmetric tensor-core tiles (fewer, longer units)
+  int tc_sym_nunits = 0, tc_sym_T = 0;
 
   // Gram-product scratch.
   float* part = nullptr;  size_t part_cap = 0;      // per-split partial sums (bytes)

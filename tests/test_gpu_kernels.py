@@ -156,6 +156,39 @@ def test_gram_full_size_sampled_rows(K_):
     assert np.max(np.abs(u32[rows] - ref)) <= 1e-5 * np.max(np.abs(ref))
 
 
+def test_rbf_full_size_sampled_rows_symmetric_tiles(K_):
+    """The n = 50000, p = 20 RBF workload on the default single-vector path
+    (symmetric tcgen05 tiles, each off-diagonal tile used for its row and its
+    column sums): sampled rows of K v against the oracle."""
+    wl = W.rbf_mid()
+    v = W.random_vectors(wl.n, seed=12)
+    rows = np.random.default_rng(6).choice(wl.n, 32, replace=False)
+    ref = O.kmatvec(wl.X, v, wl.kind, wl.gamma, rows=rows)
+    with K_.Problem(wl.X, wl.y, wl.kind, wl.gamma, rank0=16, gram_store=0) as prob:
+        u32 = prob.kmatvec(v, K_.PREC_FP32)
+    assert np.max(np.abs(u32[rows] - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("path", ["sym_tc", "plain_tc"])
+def test_rbf_tiles_without_row_folding(K_, path):
+    """One far outlier puts max_i gamma log2(e) |x_i - mean|^2 above 60, so the
+    tensor-core tiles keep exp2(-n_i) inside each entry instead of folding it
+    into the row and column factors (exp2(n_i) would overflow FP32 there)."""
+    rng = np.random.default_rng(21)
+    n, p, gamma = 1000, 10, 0.1
+    X = rng.standard_normal((n, p))
+    X[7, 0] += 25.0
+    xs2 = gamma * math.log2(math.e) * np.sum((X - X.mean(axis=0)) ** 2, axis=1)
+    assert xs2.max() > 60.0
+    y = rng.standard_normal(n)
+    with K_.Problem(X, y, "rbf", gamma, **PATHS[path]) as prob:
+        for m in (1, 3):
+            V = W.random_vectors(n, m, seed=30 + m)
+            ref = O.kmatvec(X, V, "rbf", gamma)
+            u32 = prob.kmatvec(V, K_.PREC_FP32)
+            assert np.max(np.abs(u32 - ref)) <= 1e-5 * np.max(np.abs(ref)), (m, np.max(np.abs(u32 - ref)))
+
+
 @pytest.mark.parametrize("kind,n,p", [("rbf", 2000, 10), ("laplacian", 1500, 50), ("rbf", 700, 2)])
 def test_rpcholesky_factor_and_rank_match_oracle(K_, kind, n, p):
     wl = W.rbf_small(n=n, p=p) if kind == "rbf" else W.lap_large(n=n, p=p)
