@@ -28,6 +28,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "KQR solve sec to KKT≤1e-6 at n=200k; fused K·V TFLOP/s and % of roofline"
 FP32_LANES_PER_SM = 128          # FP32 FFMA/FADD lanes per SM (measured unit rate, see the design notes)
+XU_LANES_PER_SM = 32             # MUFU (ex2) lanes per SM: the rate at which ncu's XU-pipe counter reads 100 %
+TF32_PER_BF16 = 1.1 / 2.25       # nominal dense TF32 / bf16 tensor rate
 SM_COUNT_FALLBACK = 152          # used only when the device cannot be queried
 SM_MAX_MHZ_FALLBACK = 2070.0     # used only when nvidia-smi gives no maximum clock
 # DRAM bytes (read + write) per launch of gram_f32_sym_kernel on the n = 200000, p = 50
@@ -215,6 +217,54 @@ def job_throughput_value(total_ms: float, world: int, steps: int) -> float:
     return total_ms / 1e3 / (world * steps)
 
 
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def stored_k_roofline(n: int, launches: int, ms: float) -> dict:
+    """The stored-K product reads every stored 128 x 128 FP32 tile once per launch."""
+    t = (n + 127) // 128
+    nbytes = t * (t + 1) // 2 * 128 * 128 * 4 + 8 * n
+    peak = measured_peaks().get("hbm_gbs")
+    basis = "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    if not peak:
+        peak, basis = 6800.0, "fallback 6.8 TB/s"
+    achieved = nbytes / (ms / launches / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "kstore_gemv_kernel (stored K, symmetric)", "launches": launches,
+            "avg_ms": ms / launches, "bytes_per_launch": nbytes,
+            "work_per_entry": "4 bytes per stored entry (upper-triangle tiles) + v and u", "peak_basis": basis}
+
+
+def rbf_tc_roofline(n: int, p: int, launches: int, ms: float, sm_count: int, sm_mhz: float) -> dict:
+    """The symmetric tcgen05 RBF tiles: per entry one exp2 on the MUFU (XU) pipe, three
+    FFMAs (exponent, row and column products) and 2p flops per TF32 term on the tensor
+    cores (three terms for FP32 accuracy); n(n+1)/2 entries per launch."""
+    entries = float(n) * float(n + 1) / 2.0
+    avg_s = ms / launches / 1e3
+    xu_peak = sm_count * XU_LANES_PER_SM * sm_mhz * 1e6 / 1e12          # T exp2/s
+    xu = entries / avg_s / 1e12
+    fma_peak = sm_count * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    fma = 3.0 * entries / avg_s / 1e12
+    bf16 = measured_peaks().get("bf16_tflops")
+    tf32_peak = bf16 * TF32_PER_BF16 if bf16 else 1900.0 * TF32_PER_BF16
+    tc = 6.0 * p * entries / avg_s / 1e12
+    return {"bound": "alu", "achieved": xu, "peak": xu_peak, "unit": "T exp2/s", "frac": xu / xu_peak,
+            "traffic": None, "kernel": "gram_rbf_tc_sym_kernel (tcgen05 RBF tiles, symmetric)",
+            "launches": launches, "avg_ms": ms / launches, "entries_per_launch": entries,
+            "work_per_entry": "1 exp2 (MUFU) + 3 FFMA; 6p TF32 tensor flops (three terms)",
+            "peak_basis": f"{sm_count} SMs x {XU_LANES_PER_SM} XU lanes x {sm_mhz:g} MHz; the XU rate is the one "
+                          f"at which ncu's XU-pipe utilisation of this kernel reads 100 %",
+            "fma_convention": {"achieved": fma, "peak": fma_peak, "unit": "Top/s", "frac": fma / fma_peak},
+            "tensor_convention": {"achieved": tc, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc / tf32_peak,
+                                  "peak_basis": "measured bf16 dense x nominal TF32/bf16 ratio 1.1/2.25"
+                                  + ("" if bf16 else " (fallback 1.9 PFLOP/s bf16)")}}
+
+
 def bench_config(wl, args, world: int) -> dict:
     """The bench line's config, shared by both arms."""
     return {"workload": describe(wl, args), "n": wl.n, "p": wl.p, "kernel": wl.kind, "rank0": args.rank0,
@@ -338,6 +388,7 @@ def run_ours(args):
     launches = prob.launches - launches0
     n32, ms32 = prob.profile_read(0)
     nhp, mshp = prob.profile_read(1)
+    nks, msks = prob.profile_read(2)
     prob.profile(False)
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     units = world * args.steps
@@ -374,19 +425,19 @@ def run_ours(args):
     sm_count = device_sm_count()
     sm_mhz = clk.get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK
     roofline = None
-    if n32 > 0:
+    if nks > n32:
+        roofline = stored_k_roofline(n, nks, msks)
+    elif n32 > 0 and wl.kind == "rbf":
+        roofline = rbf_tc_roofline(n, p, n32, ms32, sm_count, sm_mhz)
+    elif n32 > 0:
         avg_s = ms32 / n32 / 1e3
-        if wl.kind == "laplacian":
-            ops_per_entry = 2 * p + 2               # FADD + FADD|.| per feature; FFMA with v_j and with v_i
-            flops_per_entry = 3 * p + 4             # sub, abs, add per feature; scale, exp, multiply, add
-        else:
-            ops_per_entry = p + 4
-            flops_per_entry = 2 * p + 5
+        ops_per_entry = 2 * p + 2               # FADD + FADD|.| per feature; FFMA with v_j and with v_i
+        flops_per_entry = 3 * p + 4             # sub, abs, add per feature; scale, exp, multiply, add
         peak = sm_count * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12         # Top/s, FP32 pipe lane operations
         achieved = entries * ops_per_entry / avg_s / 1e12
         flop_peak = 2.0 * peak                                               # FFMA = 2 flops per lane and clock
         flop_achieved = entries * flops_per_entry / avg_s / 1e12
-        traffic = SYM_LAPLACIAN_TRAFFIC.get((n, p)) if wl.kind == "laplacian" else None
+        traffic = SYM_LAPLACIAN_TRAFFIC.get((n, p))
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
                     "traffic": traffic, "traffic_unit": "bytes per launch",
                     "kernel": "gram_f32_sym_kernel (FP32 Gram tiles, symmetric)",

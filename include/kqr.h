@@ -146,7 +146,10 @@ typedef struct kqr_options {
                                     1 always (kqr_create fills the packed upper triangle of K as
                                     128 x 128 FP32 tiles, (T (T + 1) / 2) * 64 KB with T = ceil(n / 128),
                                     and returns KQR_OOM if it does not fit); 2 (default) when those
-                                    bytes are at most half the free device memory at kqr_create */
+                                    bytes are at most half the free device memory at kqr_create,
+                                    except for RBF kernels with p <= 32 (tensor cores and symmetric
+                                    tiles on) once they exceed 64 MB: their on-the-fly tiles are
+                                    faster than streaming a stored K */
 } kqr_options;
 
 /* Counters and final residuals of a solve (Sec. 4 definitions). */

@@ -369,7 +369,8 @@ def test_stored_gram_matches_oracle(K_, kind, n, p):
 
 
 def test_stored_gram_falls_back_when_not_asked_or_too_large(K_):
-    """gram_store = 0 never stores; the automatic mode stores small problems."""
+    """gram_store = 0 never stores; the automatic mode stores small problems, and
+    large ones unless their on-the-fly tiles are the faster product."""
     wl = _data("rbf", 500, 4)
     with K_.Problem(wl.X, wl.y, "rbf", wl.gamma, gram_store=0) as prob:
         prob.kmatvec(W.random_vectors(500))
@@ -381,3 +382,11 @@ def test_stored_gram_falls_back_when_not_asked_or_too_large(K_):
     with K_.Problem(wl.X, wl.y, "rbf", wl.gamma) as prob:
         _, _, _, info = prob.solve(0.5, 1e-2, 1e-6)
         assert info["gram_stored"] == 1
+    # past 64 MB of stored tiles (n = 6400: 1275 tiles, 83.6 MB) the automatic mode keeps
+    # RBF kernels with p <= 32 on the symmetric tensor-core tiles, and stores Laplacian ones
+    for kind, stored in (("rbf", 0), ("laplacian", 1)):
+        wl = _data(kind, 6400, 8)
+        with K_.Problem(wl.X, wl.y, kind, wl.gamma, rank0=8) as prob:
+            prob.profile(True)
+            prob.kmatvec(W.random_vectors(6400))
+            assert prob.profile_read(2)[0] == stored, kind
