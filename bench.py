@@ -240,10 +240,11 @@ def stored_k_roofline(n: int, launches: int, ms: float) -> dict:
             "work_per_entry": "4 bytes per stored entry (upper-triangle tiles) + v and u", "peak_basis": basis}
 
 
-def rbf_tc_roofline(n: int, p: int, launches: int, ms: float, sm_count: int, sm_mhz: float) -> dict:
+def rbf_tc_roofline(n: int, p: int, launches: int, ms: float, sm_count: int, sm_mhz: float, f16: bool) -> dict:
     """The symmetric tcgen05 RBF tiles: per entry one exp2 on the MUFU (XU) pipe, three
-    FFMAs (exponent, row and column products) and 2p flops per TF32 term on the tensor
-    cores (three terms for FP32 accuracy); n(n+1)/2 entries per launch."""
+    FFMAs (exponent, row and column products) and 2p tensor flops per product term (three
+    terms for FP32 accuracy: fp16 parts when the row factors fold and 3p <= 128, else TF32
+    parts); n(n+1)/2 entries per launch."""
     entries = float(n) * float(n + 1) / 2.0
     avg_s = ms / launches / 1e3
     xu_peak = sm_count * XU_LANES_PER_SM * sm_mhz * 1e6 / 1e12          # T exp2/s
@@ -251,17 +252,20 @@ def rbf_tc_roofline(n: int, p: int, launches: int, ms: float, sm_count: int, sm_
     fma_peak = sm_count * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     fma = 3.0 * entries / avg_s / 1e12
     bf16 = measured_peaks().get("bf16_tflops")
-    tf32_peak = bf16 * TF32_PER_BF16 if bf16 else 1900.0 * TF32_PER_BF16
+    ratio = 1.0 if f16 else TF32_PER_BF16
+    tc_peak = (bf16 if bf16 else 1900.0) * ratio
     tc = 6.0 * p * entries / avg_s / 1e12
     return {"bound": "alu", "achieved": xu, "peak": xu_peak, "unit": "T exp2/s", "frac": xu / xu_peak,
             "traffic": None, "kernel": "gram_rbf_tc_sym_kernel (tcgen05 RBF tiles, symmetric)",
             "launches": launches, "avg_ms": ms / launches, "entries_per_launch": entries,
-            "work_per_entry": "1 exp2 (MUFU) + 3 FFMA; 6p TF32 tensor flops (three terms)",
+            "work_per_entry": "1 exp2 (MUFU) + 3 FFMA; 6p tensor flops (three terms, "
+                              + ("fp16 parts concatenated along K)" if f16 else "TF32 parts)"),
             "peak_basis": f"{sm_count} SMs x {XU_LANES_PER_SM} XU lanes x {sm_mhz:g} MHz; the XU rate is the one "
                           f"at which ncu's XU-pipe utilisation of this kernel reads 100 %",
             "fma_convention": {"achieved": fma, "peak": fma_peak, "unit": "Top/s", "frac": fma / fma_peak},
-            "tensor_convention": {"achieved": tc, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc / tf32_peak,
-                                  "peak_basis": "measured bf16 dense x nominal TF32/bf16 ratio 1.1/2.25"
+            "tensor_convention": {"achieved": tc, "peak": tc_peak, "unit": "TFLOP/s", "frac": tc / tc_peak,
+                                  "peak_basis": ("measured bf16 dense (fp16 runs at the bf16 rate)" if f16 else
+                                                 "measured bf16 dense x nominal TF32/bf16 ratio 1.1/2.25")
                                   + ("" if bf16 else " (fallback 1.9 PFLOP/s bf16)")}}
 
 
@@ -428,7 +432,10 @@ def run_ours(args):
     if nks > n32:
         roofline = stored_k_roofline(n, nks, msks)
     elif n32 > 0 and wl.kind == "rbf":
-        roofline = rbf_tc_roofline(n, p, n32, ms32, sm_count, sm_mhz)
+        # the library folds the row factors when every gamma log2(e) |x_i - mean|^2 < 60
+        xc = wl.X - wl.X.mean(axis=0)
+        fold = float(wl.gamma * np.log2(np.e) * np.max(np.sum(xc * xc, axis=1))) < 60.0
+        roofline = rbf_tc_roofline(n, p, n32, ms32, sm_count, sm_mhz, f16=fold and 3 * p <= 128)
     elif n32 > 0:
         avg_s = ms32 / n32 / 1e3
         ops_per_entry = 2 * p + 2               # FADD + FADD|.| per feature; FFMA with v_j and with v_i

@@ -186,7 +186,7 @@ bool make_tmap_rowmajor_bf16_sw128(CUtensorMap* tm, void* base, int64_t ldn) {
 static void free_all(Handle* h) {
   void* bufs[] = {h->xs32, h->nrm32, h->hq, h->hl, h->exp_table, h->xc64, h->y, h->F32, h->dres, h->core, h->tvec,
                   h->Linv, h->part, h->v32, h->vec_pool, h->scal, h->red_counter, h->red_part, h->err_flag,
-                  h->st_alpha, h->st_v, h->st_z, h->sym_units, h->tc_hi, h->tc_lo, h->tc_bf, h->tc_sym_units};
+                  h->st_alpha, h->st_v, h->st_z, h->sym_units, h->tc_hi, h->tc_lo, h->tc_bf, h->tc_sym_units, h->tc_a16, h->tc_b16};
   for (void* b : bufs) dev_free(h, b);
   kstore_free(h);
   batch_free(h);

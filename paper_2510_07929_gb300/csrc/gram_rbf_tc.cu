@@ -23,6 +23,7 @@
 #include <vector>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "kqr_internal.h"
 #include "ptx.cuh"
@@ -53,8 +54,9 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint6
       : "memory");
 }
 
-// D[tmem] (+)= A[smem] B[smem]^T, bf16 inputs (both), FP32 accumulate.
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+// D[tmem] (+)= A[smem] B[smem]^T, kind::f16: bf16 or fp16 inputs as the instruction
+// descriptor says (A and B of the same type), FP32 accumulate.
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(256, 1)
         const unsigned char* bl = XJl[q & 1];
         for (int k = 0; k < ksteps; ++k) {
           const uint32_t off = (uint32_t)(k >> 2) * kAtomBytes + (uint32_t)(k & 3) * 32u;
-          if (NTERMS == 0) umma_bf16(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bh + off), idesc, k > 0 ? 1u : 0u);
+          if (NTERMS == 0) umma_f16(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bh + off), idesc, k > 0 ? 1u : 0u);
           else umma_tf32(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bh + off), idesc, k > 0 ? 1u : 0u);
           if (NTERMS == 3) {
             umma_tf32(d, umma_desc_sw128(XIh + off), umma_desc_sw128(bl + off), idesc, 1u);
@@ -358,6 +360,56 @@ cudaError_t rbf_tc_prepare(Handle* h) {
   return cudaStreamSynchronize(h->stream);
 }
 
+// xs32 (feature-major [p][ldn]) -> the fp16 operands of the symmetric FP32-class tiles,
+// row-major [ldn][W] halves: per row A' = [hi | hi | lo] and B' = [hi | lo | hi] over the
+// p features (hi = fp16 round-to-nearest of x, lo = that of x - hi), zero beyond 3p.
+// A'_j . B'_i = hi_j.hi_i + hi_j.lo_i + lo_j.hi_i, the three-term product of the TF32
+// form with the same 11-bit parts, as one contraction of length 3p.
+__global__ void f16_split_kernel(const float* __restrict__ xs32, int64_t ldn, int p, int W, __half* __restrict__ a,
+                                 __half* __restrict__ b) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ldn * W; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / W;
+    const int k = (int)(e % W);
+    __half va = __float2half_rn(0.f), vb = va;
+    if (k < 3 * p) {
+      const int seg = k / p;
+      const float x = xs32[(size_t)(k % p) * ldn + i];
+      const __half hi = __float2half_rn(x);
+      const __half lo = __float2half_rn(x - __half2float(hi));
+      va = seg == 2 ? lo : hi;
+      vb = seg == 1 ? lo : hi;
+    }
+    a[e] = va;
+    b[e] = vb;
+  }
+}
+
+// Prepares the fp16 operands of the symmetric FP32-class tiles (once per problem).  Used
+// only with folded row factors (every n_i < 60, so |xs| < 8: far inside the fp16 range; a
+// lo part below 2^-14 loses bits as a subnormal, an absolute error of at most 2^-25 per
+// part, below FP32 rounding of the cross term) and 3p <= 128.
+static cudaError_t rbf_f16_prepare(Handle* h) {
+  if (h->tc_a16) return cudaSuccess;
+  const int katoms = (int)((3 * h->p + 63) / 64);
+  const int W = 64 * katoms;
+  const size_t bytes = (size_t)h->ldn * W * sizeof(__half);
+  h->tc_a16 = (float*)dev_alloc(h, bytes);
+  h->tc_b16 = (float*)dev_alloc(h, bytes);
+  if (!h->tc_a16 || !h->tc_b16) return cudaErrorMemoryAllocation;
+  h->tc16_katoms = katoms;
+  f16_split_kernel<<<grid_for(h->ldn * W), 256, 0, h->stream>>>(h->xs32, h->ldn, (int)h->p, W,
+                                                                 reinterpret_cast<__half*>(h->tc_a16),
+                                                                 reinterpret_cast<__half*>(h->tc_b16));
+  h->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // a row of W halves is W / 2 FP32 words: the same 128-byte swizzled boxes as the TF32 parts
+  if (!make_tmap_rowmajor_sw128(&h->tm_tc_a16, h->tc_a16, h->ldn, W / 2) ||
+      !make_tmap_rowmajor_sw128(&h->tm_tc_b16, h->tc_b16, h->ldn, W / 2))
+    return cudaErrorInvalidValue;
+  return cudaStreamSynchronize(h->stream);
+}
+
 template <int M, int NT>
 static cudaError_t launch_tc(Handle* h, int splits, int tps, int ksteps, cudaStream_t st) {
   const int katoms = NT == 0 ? 1 : h->tc_Kp / 32;
@@ -474,17 +526,23 @@ static cudaError_t rbf_tc_product(Handle* h, const double* V, double* U, int m, 
 // row tile I and a run of column tiles J in [J0, J1) with J0 >= I.  The MMA computes
 // D = X_J X_I^T, so TMEM lane l is row j = J*128 + l and TMEM column c is i = I*128 + c.
 //
-// One CTA = 16 warps; warp w reads TMEM lanes 32 (w mod 4) .. + 31 (the lanes its warp
-// may access) over the 32 columns 32 (w / 4) .. + 31.  Per element a thread forms
-// e = exp2(2 xs_j.xs_i - n_j [- n_i]) and adds e w_i to its row j's sum (a register sum:
-// u_J needs no exchange between threads) and e v_j to column i's sum, which stays in a
-// register across all tiles of the unit (I is fixed), so the exchange across the warp's
+// Operands (NTERMS): 3 = TF32 parts hi.hi + hi.lo + lo.hi, three MMAs per K = 8 step;
+// 16 = the same three products from fp16 parts concatenated along K (A' = [hi | hi | lo]
+// for J, B' = [hi | lo | hi] for I), one chain of ceil(3p / 16) MMAs of K = 16.  The MMAs
+// of a tile accumulate into one TMEM buffer and so run one after another; the short
+// chain of the fp16 form is what makes it faster; 1 = TF32 hi.hi alone (the TF32 product).
+//
+// One CTA = 8 warps, two CTAs per SM; warp w reads TMEM lanes 32 (w mod 4) .. + 31 (the
+// lanes its warp may access) over the 64 columns 64 (w / 4) .. + 63.  Per element a thread
+// forms e = exp2(2 xs_j.xs_i - n_j [- n_i]) and adds e w_i to its row j's sum (a register
+// sum: u_J needs no exchange between threads) and e v_j to column i's sum, which stays in
+// a register across all tiles of the unit (I is fixed), so the exchange across the warp's
 // 32 rows happens once per unit.  With FOLD (every n < 60) exp2(-n_i) is folded into
-// w_i = v_i exp2(-n_i) and exp2(-n_j) into the row and column results.
+// w_i = v_i exp2(-n_i) and into the column results.
 //
 // No CTA-wide barrier inside the tile loop: thread 0 issues the TMA copies and MMAs; a
 // copy refills a stage once the MMAs that read it have completed (mma_done), an MMA
-// reuses a TMEM buffer once all 16 warps have read it out (tmem_free, one arrival per
+// reuses a TMEM buffer once all 8 warps have read it out (tmem_free, one arrival per
 // warp).  Row sums go to the output with FP32 atomics per tile, column sums per unit.
 // Every wait is bounded; on a timeout the CTA records the error, drains its own copies
 // and MMAs (bounded) and frees its tensor memory.
@@ -569,7 +627,8 @@ __global__ void __launch_bounds__(kSymWarps * 32, 2)
     *mma_pending = -1;
     mbar_arrive_expect_tx(full_i, load_bytes);
     for (int a = 0; a < katoms; ++a) {
-      tma_load_2d(XIh + a * kAtomBytes, &tm_hi, a * 32, ti * 128, full_i);
+      // with fp16 operands tm_hi maps A' (the J rows) and tm_lo maps B' (the I rows)
+      tma_load_2d(XIh + a * kAtomBytes, NTERMS == 16 ? &tm_lo : &tm_hi, a * 32, ti * 128, full_i);
       if (NTERMS == 3) tma_load_2d(XIl + a * kAtomBytes, &tm_lo, a * 32, ti * 128, full_i);
     }
     for (int t = 0; t < nstage && t < nt; ++t) {
@@ -577,7 +636,9 @@ __global__ void __launch_bounds__(kSymWarps * 32, 2)
       *load_pending = t;
     }
   }
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  // FP32 accumulate, A and B K-major, N = 128, M = 128; operands TF32 (format 2) or fp16 (0)
+  const uint32_t idesc = (1u << 4) | (NTERMS == 16 ? 0u : (2u << 7) | (2u << 10)) | ((128u >> 3) << 17) |
+                         ((128u >> 4) << 24);
   float cacc[kSymCols];   // column sums of tile I over this warp's 32 rows, across the unit's tiles
 #pragma unroll
   for (int c = 0; c < kSymCols; ++c) cacc[c] = 0.f;
@@ -603,7 +664,8 @@ __global__ void __launch_bounds__(kSymWarps * 32, 2)
         const unsigned char* al = ah + tb;
         for (int k = 0; k < ksteps; ++k) {
           const uint32_t off = (uint32_t)(k >> 2) * kAtomBytes + (uint32_t)(k & 3) * 32u;
-          umma_tf32(d, umma_desc_sw128(ah + off), umma_desc_sw128(XIh + off), idesc, k > 0 ? 1u : 0u);
+          if (NTERMS == 16) umma_f16(d, umma_desc_sw128(ah + off), umma_desc_sw128(XIh + off), idesc, k > 0 ? 1u : 0u);
+          else umma_tf32(d, umma_desc_sw128(ah + off), umma_desc_sw128(XIh + off), idesc, k > 0 ? 1u : 0u);
           if (NTERMS == 3) {
             umma_tf32(d, umma_desc_sw128(ah + off), umma_desc_sw128(XIl + off), idesc, 1u);
             umma_tf32(d, umma_desc_sw128(al + off), umma_desc_sw128(XIh + off), idesc, 1u);
@@ -738,7 +800,8 @@ static cudaError_t tc_sym_units_ensure(Handle* h) {
 }
 cudaError_t sym_finish(Handle* h, const float* acc, double* U, const GramEpilogue& g, cudaStream_t st);
 
-// m = 1 RBF product on symmetric tensor-core tiles; nt = 3: FP32 class, 1: TF32.
+// m = 1 RBF product on symmetric tensor-core tiles; nt = 3: FP32 class (fp16 parts when
+// the row factors fold and 3p <= 128, else TF32 parts), 1: TF32.
 static cudaError_t rbf_tc_sym_product(Handle* h, const double* V, double* U, int nt, const GramEpilogue* ep,
                                       cudaStream_t st) {
   cudaError_t e = rbf_tc_prepare(h);
@@ -756,16 +819,20 @@ static cudaError_t rbf_tc_sym_product(Handle* h, const double* V, double* U, int
   GramEpilogue none;
   const GramEpilogue& g = ep ? *ep : none;
   if ((e = sym_prep(h, V, v32, acc, g.sum_p ? const_cast<double*>(g.sum_p) : nullptr, st)) != cudaSuccess) return e;
-  const int katoms = h->tc_Kp / 32;
-  const int ksteps = (int)((h->p + 7) / 8);
+  const bool f16 = nt == 3 && h->tc_fold_rows && 3 * h->p <= 128;
+  if (f16 && (e = rbf_f16_prepare(h)) != cudaSuccess) return e;
+  const int katoms = f16 ? h->tc16_katoms : h->tc_Kp / 32;
+  const int ksteps = f16 ? (int)((3 * h->p + 15) / 16) : (int)((h->p + 7) / 8);
   const size_t smem = tc_sym_smem(katoms);
-  auto kern = nt == 3 ? (h->tc_fold_rows ? gram_rbf_tc_sym_kernel<3, true> : gram_rbf_tc_sym_kernel<3, false>)
-                      : (h->tc_fold_rows ? gram_rbf_tc_sym_kernel<1, true> : gram_rbf_tc_sym_kernel<1, false>);
+  auto kern = f16 ? gram_rbf_tc_sym_kernel<16, true>
+                  : nt == 3 ? (h->tc_fold_rows ? gram_rbf_tc_sym_kernel<3, true> : gram_rbf_tc_sym_kernel<3, false>)
+                            : (h->tc_fold_rows ? gram_rbf_tc_sym_kernel<1, true> : gram_rbf_tc_sym_kernel<1, false>);
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   prof_mark(h, 0, true, st);
-  kern<<<h->tc_sym_nunits, kSymWarps * 32, smem, st>>>(h->tm_tc_hi, h->tm_tc_lo, h->nrm32, v32, h->tc_sym_units, acc,
-                                                       ksteps, katoms, tc_sym_stages(katoms), h->err_flag);
+  kern<<<h->tc_sym_nunits, kSymWarps * 32, smem, st>>>(f16 ? h->tm_tc_a16 : h->tm_tc_hi, f16 ? h->tm_tc_b16 : h->tm_tc_lo,
+                                                       h->nrm32, v32, h->tc_sym_units, acc, ksteps, katoms,
+                                                       tc_sym_stages(katoms), h->err_flag);
   prof_mark(h, 0, false, st);
   h->launches++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -124,6 +124,13 @@ struct Handle {
   CUtensorMap tm_tc_hi{}, tm_tc_lo{};
   __nv_bfloat16* tc_bf = nullptr;     // row-major bf16 copy [ldn][64] (KQR_PREC_BF16)
   CUtensorMap tm_tc_bf{};
+  // fp16 copies for the symmetric FP32-class tiles: per row A' = [hi | hi | lo] and
+  // B' = [hi | lo | hi] over the p features, zero padded to 64 tc16_katoms halves, with
+  // their swizzled tensor maps (the rows viewed as FP32 pairs).
+  float* tc_a16 = nullptr;
+  float* tc_b16 = nullptr;
+  int tc16_katoms = 0;
+  CUtensorMap tm_tc_a16{}, tm_tc_b16{};
 
   // Symmetric Gram product: work-unit table (row tile, first and end column tile).
   int4* sym_units = nullptr;
