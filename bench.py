@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "KQR solve sec to KKT≤1e-6 at n=200k; fused K·V TFLOP/s and % of roofline"
 FP32_LANES_PER_SM = 128          # FP32 FFMA/FADD lanes per SM (measured unit rate, see the design notes)
-XU_LANES_PER_SM = 32             # MUFU (ex2) lanes per SM: the rate at which ncu's XU-pipe counter reads 100 %
+XU_LANES_PER_SM = 32             # MUFU ex2 per SM and clock (microbenchmark; ncu's XU-pipe counter agrees)
 TF32_PER_BF16 = 1.1 / 2.25       # nominal dense TF32 / bf16 tensor rate
 SM_COUNT_FALLBACK = 152          # used only when the device cannot be queried
 SM_MAX_MHZ_FALLBACK = 2070.0     # used only when nvidia-smi gives no maximum clock
@@ -260,8 +260,8 @@ def rbf_tc_roofline(n: int, p: int, launches: int, ms: float, sm_count: int, sm_
             "launches": launches, "avg_ms": ms / launches, "entries_per_launch": entries,
             "work_per_entry": "1 exp2 (MUFU) + 3 FFMA; 6p tensor flops (three terms, "
                               + ("fp16 parts concatenated along K)" if f16 else "TF32 parts)"),
-            "peak_basis": f"{sm_count} SMs x {XU_LANES_PER_SM} XU lanes x {sm_mhz:g} MHz; the XU rate is the one "
-                          f"at which ncu's XU-pipe utilisation of this kernel reads 100 %",
+            "peak_basis": f"{sm_count} SMs x {XU_LANES_PER_SM} ex2 per SM and clock x {sm_mhz:g} MHz (ex2 rate from "
+                          f"a microbenchmark, consistent with ncu's XU-pipe utilisation of this kernel)",
             "fma_convention": {"achieved": fma, "peak": fma_peak, "unit": "Top/s", "frac": fma / fma_peak},
             "tensor_convention": {"achieved": tc, "peak": tc_peak, "unit": "TFLOP/s", "frac": tc / tc_peak,
                                   "peak_basis": ("measured bf16 dense (fp16 runs at the bf16 rate)" if f16 else
