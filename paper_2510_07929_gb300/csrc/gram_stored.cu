@@ -314,7 +314,7 @@ kqr_status kstore_setup(Handle* h) {
   if (mode == 2 && bytes > free_b / 2) return KQR_OK;   // automatic: only when it fits comfortably
   // automatic: once the stored tiles no longer fit in L2, the symmetric tcgen05 RBF tiles
   // (p <= 32, one 128-byte atom per row) form K faster than a stored K streams from HBM
-  // (0.53 against 0.74 ms at n = 50000)
+  // (0.48 against 0.74 ms at n = 50000)
   if (mode == 2 && h->kind == KQR_RBF && h->opt.rbf_tensor_cores && h->opt.symmetric_gram && h->p <= 32 &&
       bytes > kStoreL2Bytes)
     return KQR_OK;
