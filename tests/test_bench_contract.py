@@ -30,3 +30,30 @@ def test_reference_arm_prints_one_contract_line():
         workload, n, tol, rank0 = "rbf_small", 600, 1e-6, 1024
 
     assert d["config"] == bench.bench_config(bench.workload(A), A, 1)
+
+
+def test_roofline_helpers():
+    """The stored-K roofline counts the packed upper triangle of 128 x 128 FP32 tiles
+    plus v and u; the RBF roofline's fractions are achieved / peak on each unit, with
+    n(n+1)/2 entries per launch."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    n = 50000
+    t = (n + 127) // 128
+    r = bench.stored_k_roofline(n, launches=4, ms=4.0)
+    assert r["bound"] == "hbm" and r["bytes_per_launch"] == t * (t + 1) // 2 * 65536 + 8 * n
+    assert abs(r["achieved"] - r["bytes_per_launch"] / 1e-3 / 1e9) < 1e-6 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    entries = n * (n + 1) / 2
+    for f16 in (True, False):
+        q = bench.rbf_tc_roofline(n, 20, launches=2, ms=1.0, sm_count=152, sm_mhz=2000.0, f16=f16)
+        assert q["bound"] == "alu"
+        assert abs(q["achieved"] - entries / 0.5e-3 / 1e12) < 1e-9
+        assert abs(q["peak"] - 152 * bench.XU_LANES_PER_SM * 2000e6 / 1e12) < 1e-9
+        assert abs(q["fma_convention"]["achieved"] - 3 * entries / 0.5e-3 / 1e12) < 1e-9
+        tc = q["tensor_convention"]
+        assert abs(tc["achieved"] - 6 * 20 * entries / 0.5e-3 / 1e12) < 1e-9
+        assert abs(tc["frac"] - tc["achieved"] / tc["peak"]) < 1e-12
+    assert (bench.rbf_tc_roofline(n, 20, 2, 1.0, 152, 2000.0, True)["tensor_convention"]["peak"] >
+            bench.rbf_tc_roofline(n, 20, 2, 1.0, 152, 2000.0, False)["tensor_convention"]["peak"])
